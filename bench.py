@@ -1,0 +1,350 @@
+"""Benchmark of the UA-AMG hot path on the 3D 7-point Laplacian, 128^3 interior grid
+(2,097,152 unknowns), edge weights exp(N(0, 0.25^2)), Dirichlet, RHS uniform[-1, 1],
+solved to relative residual 1e-8.
+
+One step = the whole hot path on one system: uaamg_setup (priorities, aggregation passes,
+coarse numbering, coarse operators, smoother data, coarsest inverse) + uaamg_solve (K-cycle
+preconditioned flexible CG) + uaamg_free, inputs already resident in HBM.  The headline
+path is mixed precision (FP32 hierarchy and K-cycle inside FP64 outer iterations); the plain
+FP64 path is timed beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       (N > 1: launched by torch.distributed.run; each rank solves its own replica.)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s and p50/p99 latency to 1e-8 rel. residual, batched vs plain; setup ms"
+TOL = 1e-8
+WORKLOAD = "laplace3d_128^3 7-point, Dirichlet, lognormal(0.25) edge weights"
+
+# DRAM traffic per launch of the roofline kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {}
+
+
+def _src_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kern_solve.cu", "kern_setup.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1302_2547_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    from paper_1302_2547_gb300 import inputs as I
+
+    A = I.laplace3d_128()
+    b = I.rhs_uniform(A.n, I.RHS_SEED + 1)
+    return A, b
+
+
+def bench_params(U, precision, profile_class=0):
+    return U.uaamg_default_params(precision=precision, max_agg_size=0,
+                                  profile_class=profile_class)
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_1302_2547_gb300 import _lib as U
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    A, b = workload()
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        rp, cc, vv = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+        bd = torch.from_numpy(b).to(dev)
+        xd = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    stream.synchronize()
+    Asp = None
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    def one_step(precision, profile_class=0):
+        h = U.uaamg_setup(rp, cc, vv, bench_params(U, precision, profile_class), stream=stream)
+        try:
+            if profile_class in (U.UAAMG_KCLASS_SMOOTH0, U.UAAMG_KCLASS_SPMV64):
+                U.uaamg_set_profiling(h, profile_class)
+            st, it, rr = U.uaamg_solve(h, bd, xd, TOL)
+            if st != 0:
+                raise RuntimeError(f"solve status {st} after {it} iterations, relres {rr}")
+            s = U.uaamg_get_stats(h)
+            prof = U.uaamg_get_profile(h) if profile_class else None
+            return it, rr, s, prof
+        finally:
+            U.uaamg_free(h)
+
+    def timed(precision, K, W, profile_class=0, sampler=None):
+        for _ in range(W):
+            one_step(precision)
+        barrier()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        rec = []
+        l0 = U.uaamg_total_launches()
+        if sampler:
+            sampler.__enter__()
+        ev[0].record(stream)
+        for k in range(K):
+            rec.append(one_step(precision, profile_class))
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.__exit__()
+        launches = U.uaamg_total_launches() - l0
+        barrier()
+        lat = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+        total = ev[0].elapsed_time(ev[K])
+        return total, lat, rec, launches
+
+    # headline: mixed precision, with the roofline kernel's own events live in the timed region
+    prof_cls = {"smooth0": U.UAAMG_KCLASS_SMOOTH0, "spmv64": U.UAAMG_KCLASS_SPMV64,
+                "paa": U.UAAMG_KCLASS_PAA, "coarse": U.UAAMG_KCLASS_COARSE}[args.roofline_kernel]
+    sampler = ClockSampler(dev.index)
+    total_ms, lat, rec, launches = timed(U.UAAMG_MIXED, args.steps, args.warmup, prof_cls, sampler)
+    # the plain one-at-a-time FP64 GPU path, same workload
+    p_total, p_lat, p_rec, _ = timed(U.UAAMG_FP64, max(2, args.steps // 2), 1)
+
+    # check the last solution on the host in FP64
+    import scipy.sparse as sp
+
+    Asp = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+    xh = xd.cpu().numpy()
+    relres_host = float(np.linalg.norm(b - Asp @ xh) / np.linalg.norm(b))
+
+    t_local = total_ms / 1000.0
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_local = float(t.item())
+    value = args.steps * world / t_local
+
+    # end to end through the C ABI from pinned host buffers (rank-local, then max)
+    e2e = None
+    if not args.skip_e2e:
+        rp_h = torch.from_numpy(A.rowptr).pin_memory().numpy()
+        cc_h = torch.from_numpy(A.col).pin_memory().numpy()
+        vv_h = torch.from_numpy(A.val).pin_memory().numpy()
+        b_h = torch.from_numpy(b).pin_memory().numpy()
+        x_h = torch.zeros(A.n, dtype=torch.float64).pin_memory().numpy()
+        Ke = max(2, args.steps // 2)
+        for k in range(Ke + 1):
+            if k == 1:
+                torch.cuda.synchronize()
+                barrier()
+                t0 = time.perf_counter()
+            h = U.uaamg_setup(rp_h, cc_h, vv_h, bench_params(U, U.UAAMG_MIXED), stream=stream)
+            st, it, rr = U.uaamg_solve(h, b_h, x_h, TOL)
+            U.uaamg_free(h)
+            assert st == 0
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        h2d = A.rowptr.nbytes + A.col.nbytes + A.val.nbytes + b.nbytes
+        e2e = {"value": Ke * world / te, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(x_h.nbytes)}
+
+    its = [r[0] for r in rec]
+    stats = rec[-1][2]
+    prof = [r[3] for r in rec if r[3]]
+    n_launch = sum(p[0] for p in prof)
+    ms_launch = sum(p[1] for p in prof)
+    bytes_launch = prof[-1][2] if prof else 0.0
+    peaks, peak_src = _peaks()
+    roof = None
+    if n_launch and ms_launch > 0:
+        avg_s = ms_launch / n_launch / 1000.0
+        achieved = bytes_launch / avg_s / 1e9
+        traffic = NCU_TRAFFIC.get((args.roofline_kernel, _src_hash()))
+        roof = {"bound": "hbm", "kernel": args.roofline_kernel, "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy)"
+                if peak_src == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": bytes_launch, "launches_timed": n_launch,
+                "avg_launch_us": round(avg_s * 1e6, 2)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded generator; no dataset)",
+        "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "tol": TOL,
+                   "precision": "FP32 hierarchy + K-cycle, FP64 outer flexible CG",
+                   "max_agg_size": 0, "pass_mode": "single round (Algorithm 2)",
+                   "l2": "inputs larger than L2 (CSR 183 MB FP64 > 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "setup_ms": round(float(np.median([r[2]['setup_ms'] for r in rec])), 3),
+        "solve_ms": round(float(np.median([r[2]['solve_ms'] for r in rec])), 3),
+        "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                       "p99": round(float(np.percentile(lat, 99)), 3)},
+        "iterations": int(np.median(its)), "relres_host_fp64": relres_host,
+        "levels": None, "opc": round(stats["opc"], 3),
+        "plain_fp64": {"value": round(len(p_lat) / (p_total / 1000.0), 3), "unit": "solves/s",
+                       "setup_ms": round(float(np.median([r[2]['setup_ms'] for r in p_rec])), 3),
+                       "solve_ms": round(float(np.median([r[2]['solve_ms'] for r in p_rec])), 3),
+                       "iterations": int(np.median([r[0] for r in p_rec]))},
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+        "clocks": sampler.summary(),
+    }
+    return out
+
+
+def run_cpu_baseline(sample_steps=1):
+    """The oracle as it stands (serial C, FP64) on the same workload: setup + solve."""
+    from oracle import oracle as O
+
+    O.build()
+    A, b = workload()
+    t = []
+    for _ in range(sample_steps):
+        t0 = time.perf_counter()
+        H = O.Hierarchy(A.rowptr, A.col, A.val, O.Params(max_agg_size=0))
+        x, it, rr, st, _ = H.solve(b, TOL)
+        t.append(time.perf_counter() - t0)
+        assert st == 0
+        del H
+    return {"value": round(len(t) / sum(t), 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(t)} full setup+solve of the 128^3 system (serial C, FP64), "
+                      f"{sum(t):.1f} s"}, t, it
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="uaamg", choices=["uaamg", "reference"])
+    ap.add_argument("--roofline-kernel", default="smooth0",
+                    choices=["smooth0", "spmv64", "paa", "coarse"])
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        W, K = args.warmup, args.steps
+        for _ in range(W):
+            run_cpu_baseline(1)
+        base, t, it = run_cpu_baseline(K)
+        value = base["value"]
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": round(1000 * sum(t) / K, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator; no dataset)",
+            "config": {"workload": WORKLOAD, "tol": TOL, "max_agg_size": 0},
+            "iterations": it, "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1302_2547_gb300 import build as B
+
+    if rank == 0:
+        B.build()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    out = run_gpu(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.skip_cpu_baseline:
+            out["cpu_baseline"] = run_cpu_baseline(1)[0]
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * uaamg.h -- C ABI of the GB300 (sm_103a) unsmoothed-aggregation AMG library.
+ *
+ * The library solves A u = f (Eq. 2.1) for a weighted graph Laplacian A (Section 2):
+ * symmetric, a_ij = -w_ij <= 0 off the diagonal, a_ii = sum_j w_ij + wD_i, positive definite
+ * because a Dirichlet set S is non-empty on every connected component.
+ *
+ *   setup (Algorithm 1, setup phase): per level, priorities (Eq. 3.2), parallel aggregation
+ *     passes (Algorithm 2), coarse numbering by ascending root (Section 5.1), coarse
+ *     operator by aggregate sums (Eq. 2.4), l1-Jacobi data (Section 4.1), and a dense
+ *     Cholesky-based inverse of the coarsest matrix.
+ *   solve (Algorithm 1, solve phase, with the K-cycle of Section 4.3 as preconditioner of
+ *     a flexible conjugate gradient, Sections 1 and 4.4): l1-Jacobi smoothing fused into
+ *     CSR SpMV, aggregate-sum restriction and piecewise-constant prolongation
+ *     (Section 4.2), two flexible-CG steps per coarse level.
+ *
+ * Every compute step runs in this library's CUDA kernels on the caller's stream.  There is
+ * no CPU fallback: without a usable CUDA device every call that computes returns
+ * UAAMG_ERR_CUDA.
+ *
+ * Conventions
+ *  - Indices are 0-based int32.  CSR: rowptr[n+1], col[nnz] strictly ascending within each
+ *    row, the diagonal stored, val[nnz] float64.  The pattern and values must be
+ *    symmetric; the diagonal must be positive.
+ *  - Pointers are host or device addresses as stated per argument.  The library never
+ *    keeps a caller pointer after a call returns.
+ *  - Every function returns a status code (UAAMG_OK = 0) and never throws.  On an error
+ *    the output arguments are unspecified unless stated.
+ *  - A handle is used by one host thread at a time and runs all its work on the stream
+ *    given at setup; different handles may run concurrently on different streams.
+ */
+#ifndef UAAMG_H
+#define UAAMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------- */
+#define UAAMG_OK 0
+#define UAAMG_ERR_INVALID_ARG 1   /* null pointer, out-of-range parameter */
+#define UAAMG_ERR_BAD_CSR 2       /* malformed, unsorted, asymmetric, non-finite, bad diag */
+#define UAAMG_ERR_NOT_SPD 3       /* Cholesky breakdown on the coarsest level */
+#define UAAMG_ERR_NO_CONVERGENCE 4 /* max_iter reached; iters/relres/x are still filled */
+#define UAAMG_ERR_OOM 5           /* device allocation failed */
+#define UAAMG_ERR_BUDGET 6        /* the library-wide device-memory budget would be exceeded */
+#define UAAMG_ERR_CUDA 7          /* a CUDA runtime call failed (no device, launch error) */
+#define UAAMG_ERR_TIMEOUT 8       /* a bounded device-side wait gave up */
+#define UAAMG_ERR_UNSUPPORTED 9   /* a size beyond this build's limits */
+
+/* ---- parameters --------------------------------------------------------------------- */
+#define UAAMG_FP64 0  /* K-cycle, hierarchy and outer iteration in FP64 */
+#define UAAMG_MIXED 1 /* FP32 hierarchy and K-cycle inside the FP64 outer iteration */
+
+#define UAAMG_PASS_SINGLE_ROUND 1 /* Algorithm 2 as printed: one round of local maxima per pass */
+#define UAAMG_PASS_MAXIMAL 0      /* a maximal distance-2 independent set per pass (Section 3.1) */
+
+typedef struct uaamg_csr {
+    int32_t n;             /* rows = columns, >= 1 */
+    int32_t nnz;           /* stored entries, rowptr[n] */
+    const int32_t* rowptr; /* [n+1] */
+    const int32_t* col;    /* [nnz] */
+    const double* val;     /* [nnz] */
+    int32_t on_device;     /* 1: the three arrays are device pointers, 0: host pointers */
+} uaamg_csr;
+
+typedef struct uaamg_params {
+    int32_t coarse_size;  /* coarsen while n_l > coarse_size (Algorithm 1 "n_0"); default 64 */
+    int32_t max_levels;   /* at most this many levels, finest included (Algorithm 1 "L"); 25 */
+    int32_t max_agg_size; /* t of Section 3.3: 0 = unbounded, else >= 2; default 5 */
+    int32_t pass_mode;    /* UAAMG_PASS_SINGLE_ROUND (default) or UAAMG_PASS_MAXIMAL */
+    uint64_t seed;        /* seed of the hashed priority vector (Eq. 3.2); default 0x5EED */
+    int32_t pre, post;    /* l1-Jacobi sweeps before / after the coarse correction; 1, 1 */
+    int32_t kcycle_inner; /* flexible-CG steps per coarse level, 1 or 2; default 2 */
+    double kcycle_tau;    /* > 0: skip the second step when |rho~| <= tau |rho|; default 0 */
+    int32_t precision;    /* UAAMG_MIXED (default) or UAAMG_FP64 */
+    int32_t max_iter;     /* outer iterations; default 200 */
+    int32_t use_graphs;   /* 1 (default): replay each outer iteration as a CUDA graph */
+    int32_t profile_class; /* UAAMG_KCLASS_* to time from setup on (0 = none, default) */
+} uaamg_params;
+
+typedef struct uaamg_handle uaamg_handle;
+
+/* Fills *p with the defaults listed above. */
+void uaamg_default_params(uaamg_params* p);
+
+/*
+ * Setup phase of Algorithm 1 for the matrix A on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  The CSR is validated on the device (UAAMG_ERR_BAD_CSR), copied
+ * into handle-owned device memory, and the hierarchy is built: levels 0 (finest) .. L-1
+ * (coarsest, n <= 1024 or UAAMG_ERR_UNSUPPORTED).  The caller's arrays may be freed or
+ * reused when the call returns.  The call synchronises `stream` a few times per level to
+ * learn level sizes.  On success *out owns all device memory of the hierarchy until
+ * uaamg_free; on failure *out is NULL.
+ */
+int uaamg_setup(const uaamg_csr* A, const uaamg_params* p, void* stream, uaamg_handle** out);
+
+/*
+ * Solves A x = b by flexible CG preconditioned with the K-cycle until
+ * |b - A x|_2 <= tol |b|_2 for the recomputed FP64 residual, or max_iter iterations.
+ * b[n] and x[n] are float64, host or device pointers (detected per call).  use_guess != 0
+ * takes the initial x from x, else x0 = 0.  On return x holds the last iterate, *iters the
+ * outer iteration count and *relres the final relative residual (both filled also for
+ * UAAMG_ERR_NO_CONVERGENCE).  The call synchronises the handle's stream once per outer
+ * iteration.
+ */
+int uaamg_solve(uaamg_handle* h, const double* b, double* x, double tol, int32_t use_guess,
+                int32_t* iters, double* relres);
+
+/* Releases every device allocation of the handle (stream-ordered on its stream). */
+void uaamg_free(uaamg_handle* h);
+
+/* ---- introspection, used by the parity tests ---------------------------------------- */
+int uaamg_num_levels(const uaamg_handle* h, int32_t* nlev);
+/* n, nnz and the number of aggregation passes of level l (passes = 0 on the coarsest). */
+int uaamg_level_info(const uaamg_handle* h, int32_t l, int32_t* n, int32_t* nnz,
+                     int32_t* passes);
+/* Host copies: agg[n_l] (column of P holding each row, l < L-1), and the level matrix. */
+int uaamg_get_aggregates(const uaamg_handle* h, int32_t l, int32_t* agg);
+int uaamg_get_level_csr(const uaamg_handle* h, int32_t l, int32_t* rowptr, int32_t* col,
+                        double* val);
+/* Host copies of the priority vector (Eq. 3.2) of level l and of the pass in which each
+ * vertex was aggregated (l < L-1). */
+int uaamg_get_priorities(const uaamg_handle* h, int32_t l, uint64_t* P);
+int uaamg_get_pass_of(const uaamg_handle* h, int32_t l, int32_t* pass_of);
+/* Host copy of the FP64 l1-Jacobi diagonal Minv_i = 1 / (a_ii + sum_{j!=i} |a_ij|). */
+int uaamg_get_minv(const uaamg_handle* h, int32_t l, double* minv);
+/* Applies the level-l preconditioner B_l (l < L-1) or the level-m K-cycle K_m (m >= 1) to a
+ * host vector in the handle's precision; out and in are host float64 arrays of n_l. */
+int uaamg_apply_B(uaamg_handle* h, int32_t l, const double* in, double* out);
+int uaamg_apply_K(uaamg_handle* h, int32_t m, const double* in, double* out);
+/* Relative residual |b - A x| / |b| after each outer iteration of the last solve
+ * (hist[0] = initial); *count receives min(cap, iterations + 1). */
+int uaamg_residual_history(const uaamg_handle* h, double* hist, int32_t cap, int32_t* count);
+
+/* ---- measurement -------------------------------------------------------------------- */
+typedef struct uaamg_stats {
+    double setup_ms;      /* device time of the last setup (CUDA events) */
+    double solve_ms;      /* device time of the last solve */
+    int64_t launches;     /* kernels launched by this handle (graph nodes counted per replay) */
+    int64_t graph_nodes;  /* kernel nodes of one outer-iteration graph */
+    double opc;           /* operator complexity sum_l nnz_l / nnz_0 */
+    double grid_complexity;
+} uaamg_stats;
+int uaamg_get_stats(const uaamg_handle* h, uaamg_stats* s);
+
+/*
+ * Kernel timing hooks.  When enabled (params.profile_class at setup for the setup classes,
+ * or uaamg_set_profiling before the first solve of a handle), every level-0
+ * launch of the selected kernel class is bracketed by CUDA events on the launching stream
+ * (inside the captured graphs as well), and the durations accumulate.
+ */
+#define UAAMG_KCLASS_SMOOTH0 1  /* level-0 fused SpMV + l1-Jacobi kernels of the K-cycle */
+#define UAAMG_KCLASS_SPMV64 2   /* level-0 FP64 SpMV + dot kernel of the outer iteration */
+#define UAAMG_KCLASS_PAA 3      /* the aggregation kernel of setup level 0 */
+#define UAAMG_KCLASS_COARSE 4   /* the coarse-operator assembly kernel of setup level 0 */
+int uaamg_set_profiling(uaamg_handle* h, int32_t kclass);
+/* launches, total ms, and algorithmic bytes moved per launch of the profiled class */
+int uaamg_get_profile(const uaamg_handle* h, int64_t* launches, double* total_ms,
+                      double* bytes_per_launch);
+
+/* Total kernels launched by this library in this process (all handles). */
+int64_t uaamg_total_launches(void);
+/* Library-wide cap on device bytes held by all handles (0 = no cap), and the bytes held. */
+int uaamg_set_memory_budget(uint64_t bytes);
+uint64_t uaamg_memory_in_use(void);
+
+const char* uaamg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UAAMG_H */

@@ -1,0 +1,264 @@
+"""ctypes binding of libuaamg (include/uaamg.h): the same entry points, argument
+marshalling only.  Arrays may be numpy arrays (host) or torch tensors (host or CUDA);
+every computation runs in the library's CUDA kernels.  Importing this module does not load
+the library; the first call does, and raises if the CUDA library has not been built."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libuaamg.so")
+
+UAAMG_OK = 0
+UAAMG_ERR_NO_CONVERGENCE = 4
+UAAMG_FP64, UAAMG_MIXED = 0, 1
+UAAMG_PASS_MAXIMAL, UAAMG_PASS_SINGLE_ROUND = 0, 1
+UAAMG_KCLASS_SMOOTH0, UAAMG_KCLASS_SPMV64, UAAMG_KCLASS_PAA, UAAMG_KCLASS_COARSE = 1, 2, 3, 4
+
+# every symbol declared in include/uaamg.h
+EXPORTS = [
+    "uaamg_default_params", "uaamg_setup", "uaamg_solve", "uaamg_free", "uaamg_num_levels",
+    "uaamg_level_info", "uaamg_get_aggregates", "uaamg_get_level_csr", "uaamg_get_priorities",
+    "uaamg_get_pass_of", "uaamg_get_minv", "uaamg_apply_B", "uaamg_apply_K",
+    "uaamg_residual_history", "uaamg_get_stats", "uaamg_set_profiling", "uaamg_get_profile",
+    "uaamg_total_launches", "uaamg_set_memory_budget", "uaamg_memory_in_use",
+    "uaamg_status_string",
+]
+
+
+class uaamg_csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class uaamg_params(C.Structure):
+    _fields_ = [("coarse_size", C.c_int32), ("max_levels", C.c_int32),
+                ("max_agg_size", C.c_int32), ("pass_mode", C.c_int32), ("seed", C.c_uint64),
+                ("pre", C.c_int32), ("post", C.c_int32), ("kcycle_inner", C.c_int32),
+                ("kcycle_tau", C.c_double), ("precision", C.c_int32), ("max_iter", C.c_int32),
+                ("use_graphs", C.c_int32), ("profile_class", C.c_int32)]
+
+
+class uaamg_stats(C.Structure):
+    _fields_ = [("setup_ms", C.c_double), ("solve_ms", C.c_double), ("launches", C.c_int64),
+                ("graph_nodes", C.c_int64), ("opc", C.c_double),
+                ("grid_complexity", C.c_double)]
+
+
+class UaamgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Loads libuaamg.so; raises when it has not been built (there is no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libuaamg.so is not built ({LIB_PATH}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        P, I32, I64, U64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+        sig = {
+            "uaamg_default_params": (None, [C.POINTER(uaamg_params)]),
+            "uaamg_setup": (C.c_int, [C.POINTER(uaamg_csr), C.POINTER(uaamg_params), P,
+                                      C.POINTER(P)]),
+            "uaamg_solve": (C.c_int, [P, P, P, D, I32, C.POINTER(I32), C.POINTER(D)]),
+            "uaamg_free": (None, [P]),
+            "uaamg_num_levels": (C.c_int, [P, C.POINTER(I32)]),
+            "uaamg_level_info": (C.c_int, [P, I32, C.POINTER(I32), C.POINTER(I32),
+                                           C.POINTER(I32)]),
+            "uaamg_get_aggregates": (C.c_int, [P, I32, P]),
+            "uaamg_get_level_csr": (C.c_int, [P, I32, P, P, P]),
+            "uaamg_get_priorities": (C.c_int, [P, I32, P]),
+            "uaamg_get_pass_of": (C.c_int, [P, I32, P]),
+            "uaamg_get_minv": (C.c_int, [P, I32, P]),
+            "uaamg_apply_B": (C.c_int, [P, I32, P, P]),
+            "uaamg_apply_K": (C.c_int, [P, I32, P, P]),
+            "uaamg_residual_history": (C.c_int, [P, P, I32, C.POINTER(I32)]),
+            "uaamg_get_stats": (C.c_int, [P, C.POINTER(uaamg_stats)]),
+            "uaamg_set_profiling": (C.c_int, [P, I32]),
+            "uaamg_get_profile": (C.c_int, [P, C.POINTER(I64), C.POINTER(D), C.POINTER(D)]),
+            "uaamg_total_launches": (I64, []),
+            "uaamg_set_memory_budget": (C.c_int, [U64]),
+            "uaamg_memory_in_use": (U64, []),
+            "uaamg_status_string": (C.c_char_p, [C.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().uaamg_status_string(status).decode()
+
+
+def check(status: int, where: str = "uaamg") -> int:
+    if status != UAAMG_OK:
+        raise UaamgError(status, where)
+    return status
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or torch tensor (contiguous)."""
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data, 0
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):  # torch.cuda.Stream
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def uaamg_default_params(**overrides) -> uaamg_params:
+    p = uaamg_params()
+    lib().uaamg_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def uaamg_setup(rowptr, col, val, params: uaamg_params | None = None, stream=None):
+    """Returns a handle (c_void_p).  rowptr/col int32, val float64; all host or all device."""
+    (rp, d0), (cp, d1), (vp, d2) = _ptr(rowptr), _ptr(col), _ptr(val)
+    if not (d0 == d1 == d2):
+        raise ValueError("rowptr, col and val must all be host or all device arrays")
+    n = int(rowptr.shape[0]) - 1
+    A = uaamg_csr(n, int(col.shape[0]), rp, cp, vp, d0)
+    h = C.c_void_p()
+    check(lib().uaamg_setup(C.byref(A), C.byref(params) if params is not None else None,
+                            _stream(stream), C.byref(h)), "uaamg_setup")
+    return h
+
+
+def uaamg_solve(h, b, x, tol: float = 1e-8, use_guess: bool = False):
+    """Returns (status, iters, relres); status may be UAAMG_ERR_NO_CONVERGENCE."""
+    it, rr = C.c_int32(0), C.c_double(0.0)
+    st = lib().uaamg_solve(h, _ptr(b)[0], _ptr(x)[0], tol, int(use_guess), C.byref(it),
+                           C.byref(rr))
+    if st not in (UAAMG_OK, UAAMG_ERR_NO_CONVERGENCE):
+        check(st, "uaamg_solve")
+    return st, int(it.value), float(rr.value)
+
+
+def uaamg_free(h):
+    if h:
+        lib().uaamg_free(h)
+
+
+def uaamg_num_levels(h) -> int:
+    v = C.c_int32(0)
+    check(lib().uaamg_num_levels(h, C.byref(v)), "uaamg_num_levels")
+    return v.value
+
+
+def uaamg_level_info(h, l: int):
+    n, z, p = C.c_int32(), C.c_int32(), C.c_int32()
+    check(lib().uaamg_level_info(h, l, C.byref(n), C.byref(z), C.byref(p)), "uaamg_level_info")
+    return n.value, z.value, p.value
+
+
+def uaamg_get_aggregates(h, l: int) -> np.ndarray:
+    n, _, _ = uaamg_level_info(h, l)
+    a = np.empty(n, np.int32)
+    check(lib().uaamg_get_aggregates(h, l, a.ctypes.data), "uaamg_get_aggregates")
+    return a
+
+
+def uaamg_get_level_csr(h, l: int):
+    n, z, _ = uaamg_level_info(h, l)
+    rp, cc, vv = np.empty(n + 1, np.int32), np.empty(z, np.int32), np.empty(z)
+    check(lib().uaamg_get_level_csr(h, l, rp.ctypes.data, cc.ctypes.data, vv.ctypes.data),
+          "uaamg_get_level_csr")
+    return rp, cc, vv
+
+
+def uaamg_get_priorities(h, l: int) -> np.ndarray:
+    n, _, _ = uaamg_level_info(h, l)
+    a = np.empty(n, np.uint64)
+    check(lib().uaamg_get_priorities(h, l, a.ctypes.data), "uaamg_get_priorities")
+    return a
+
+
+def uaamg_get_pass_of(h, l: int) -> np.ndarray:
+    n, _, _ = uaamg_level_info(h, l)
+    a = np.empty(n, np.int32)
+    check(lib().uaamg_get_pass_of(h, l, a.ctypes.data), "uaamg_get_pass_of")
+    return a
+
+
+def uaamg_get_minv(h, l: int) -> np.ndarray:
+    n, _, _ = uaamg_level_info(h, l)
+    a = np.empty(n)
+    check(lib().uaamg_get_minv(h, l, a.ctypes.data), "uaamg_get_minv")
+    return a
+
+
+def uaamg_apply_B(h, l: int, v) -> np.ndarray:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.empty_like(v)
+    check(lib().uaamg_apply_B(h, l, v.ctypes.data, out.ctypes.data), "uaamg_apply_B")
+    return out
+
+
+def uaamg_apply_K(h, m: int, v) -> np.ndarray:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.empty_like(v)
+    check(lib().uaamg_apply_K(h, m, v.ctypes.data, out.ctypes.data), "uaamg_apply_K")
+    return out
+
+
+def uaamg_residual_history(h, cap: int = 4096) -> np.ndarray:
+    a = np.empty(cap)
+    k = C.c_int32(0)
+    check(lib().uaamg_residual_history(h, a.ctypes.data, cap, C.byref(k)),
+          "uaamg_residual_history")
+    return a[: k.value].copy()
+
+
+def uaamg_get_stats(h) -> dict:
+    s = uaamg_stats()
+    check(lib().uaamg_get_stats(h, C.byref(s)), "uaamg_get_stats")
+    return {k: getattr(s, k) for k, _ in uaamg_stats._fields_}
+
+
+def uaamg_set_profiling(h, kclass: int):
+    check(lib().uaamg_set_profiling(h, kclass), "uaamg_set_profiling")
+
+
+def uaamg_get_profile(h):
+    n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+    check(lib().uaamg_get_profile(h, C.byref(n), C.byref(ms), C.byref(by)), "uaamg_get_profile")
+    return n.value, ms.value, by.value
+
+
+def uaamg_total_launches() -> int:
+    return int(lib().uaamg_total_launches())
+
+
+def uaamg_set_memory_budget(nbytes: int):
+    check(lib().uaamg_set_memory_budget(nbytes), "uaamg_set_memory_budget")
+
+
+def uaamg_memory_in_use() -> int:
+    return int(lib().uaamg_memory_in_use())

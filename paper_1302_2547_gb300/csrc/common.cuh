@@ -1,0 +1,246 @@
+// common.cuh -- types and device helpers shared by the CUDA sources of libuaamg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <utility>
+#include <vector>
+
+#include "uaamg.h"
+
+namespace uaamg {
+
+constexpr int kMaxLevels = 64;
+constexpr int kMaxCoarsest = 1024;        // dense inverse of the coarsest level
+constexpr int kMaxRoundSlots = 1 << 16;   // aggregation rounds + passes per level
+constexpr int kThreads = 256;             // block size of every row / element kernel
+constexpr int kRowsPerBlock = 256;        // rows of one row-block SpMV block
+constexpr int kChunk = 2048;              // matrix entries staged in shared memory per step
+constexpr long long kBarrierTimeoutNs = 2000000000LL;  // bounded grid-barrier wait
+
+// error bits raised by device code into Ctrl::err
+constexpr int kErrTimeout = 1;
+constexpr int kErrNotSpd = 2;
+constexpr int kErrBadCsr = 4;
+constexpr int kErrSlots = 8;
+
+// vertex states of the aggregation passes (Algorithm 2)
+constexpr uint8_t ST_CAND = 0;  // unprocessed, still a candidate of this pass
+constexpr uint8_t ST_EXCL = 1;  // unprocessed, within distance 2 of a root of this pass
+constexpr uint8_t ST_ROOT = 2;  // coarse vertex chosen in this pass
+constexpr uint8_t ST_DONE = 3;  // processed (in an aggregate)
+
+// Device-resident control words of a handle.
+struct Ctrl {
+    int skip;                // level+1 of the K-cycle level skipping its second step, else 0
+    int err;                 // kErr* bits
+    unsigned int red_count;  // arrival counter of the last-block reductions
+    unsigned int bar_count;  // grid barrier arrivals
+    unsigned int bar_gen;    // grid barrier generation
+    int npasses;             // written by the aggregation kernel
+    int pad[2];
+};
+
+// FP64 scalars of one K-cycle level (Section 4.3).  Step 1 writes (rho1, alpha1), step 2
+// writes (beta, gamma, alpha2) contiguously, matching the dot order of the fused kernels.
+struct LevelScalars {
+    double rho1, alpha1, beta, gamma, alpha2, rtrt, rhorho;
+    int skip2;  // 1 when this level's second step is skipped
+    int pad;
+};
+
+// FP64 scalars of the outer flexible CG.
+struct OuterScalars {
+    double pq, pr;  // written together by the fused SpMV + dots
+    double zq;
+    double rr;
+    double bb;
+    double pq_prev;
+    double alpha;
+    int first;      // 1 until the first direction update
+    int breakdown;  // (p, A p) <= 0 seen
+};
+
+struct Level {
+    int n = 0;
+    long long nnz = 0;
+    int* rowptr = nullptr;
+    int* col = nullptr;
+    double* val64 = nullptr;
+    float* val32 = nullptr;
+    double* minv64 = nullptr;
+    float* minv32 = nullptr;
+    uint64_t* prio = nullptr;
+    int* pass_of = nullptr;
+    int* agg = nullptr;      // fine -> coarse (absent on the coarsest)
+    int nc = 0;
+    int* aggptr = nullptr;   // [nc+1] members of each aggregate, ascending
+    int* members = nullptr;  // [n]
+    int passes = 0;
+    // K-cycle workspace in the handle's precision
+    void *rhs = nullptr, *out = nullptr, *w = nullptr, *s = nullptr;
+    void *c1 = nullptr, *v1 = nullptr, *rt = nullptr, *c2 = nullptr, *v2 = nullptr;
+    LevelScalars* sc = nullptr;
+};
+
+struct ProfSlot {
+    cudaEvent_t a, b;
+};
+
+struct Handle {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t user = nullptr;  // caller's stream
+    cudaStream_t work = nullptr;  // the handle's own stream (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    uaamg_params p{};
+    int nlev = 0;
+    Level lev[kMaxLevels];
+    double* coarse_inv = nullptr;  // dense inverse of the coarsest matrix (FP64)
+    int nco = 0;
+    // outer iteration vectors (FP64)
+    double *b = nullptr, *x = nullptr, *r = nullptr, *p_ = nullptr, *q = nullptr;
+    OuterScalars* osc = nullptr;
+    OuterScalars* osc_host = nullptr;  // pinned mirror
+    Ctrl* ctrl = nullptr;
+    double* partials = nullptr;
+    size_t partials_cap = 0;
+    // graph of one outer iteration
+    cudaGraphExec_t graph = nullptr;
+    long long graph_nodes = 0;
+    // stats
+    double setup_ms = 0, solve_ms = 0;
+    long long launches = 0;
+    std::vector<double> hist;
+    // profiling
+    int prof_class = 0;
+    std::vector<ProfSlot> prof_slots;
+    long long prof_launches = 0;
+    double prof_ms = 0, prof_bytes = 0;
+    // allocations
+    std::vector<void*> allocs;
+    std::vector<std::pair<void*, size_t>> temps;  // setup scratch, released when setup ends
+    size_t bytes = 0;
+    bool capturing = false;
+};
+
+// ---- host helpers (defined in runtime.cu) ------------------------------------------------
+int check_cuda(cudaError_t e);
+void* dalloc_bytes(Handle* h, size_t bytes, int* status, bool temp = false);
+template <typename T>
+T* dalloc(Handle* h, size_t count, int* status, bool temp = false) {
+    return static_cast<T*>(dalloc_bytes(h, sizeof(T) * (count ? count : 1), status, temp));
+}
+void dfree_temps(Handle* h);
+void dfree_all(Handle* h);
+void count_launch(Handle* h, long long k = 1);
+int grid_for(long long items, int per_block);
+
+// ---- device helpers ---------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperatively launched kernel (all blocks co-resident).  The
+// wait is bounded: after kBarrierTimeoutNs the block records kErrTimeout and leaves; the
+// caller then stops.  Returns false once any block has timed out.
+__device__ __forceinline__ bool grid_barrier(Ctrl* c) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &c->bar_gen;
+        unsigned int g = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&c->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            long long t0 = global_ns();
+            while (*vgen == g) {
+                if (global_ns() - t0 > kBarrierTimeoutNs) {
+                    atomicOr(&c->err, kErrTimeout);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return (*(volatile int*)&c->err & kErrTimeout) == 0;
+}
+
+// Deterministic reduction of ND per-thread values over the whole grid: each block reduces
+// with a fixed tree and stores its partials; the last block to arrive adds the partials in
+// block order and writes result[0..ND).  Every thread of every block must call it.
+template <int ND>
+__device__ __forceinline__ void grid_reduce(const double (&v)[ND], double* partials,
+                                            unsigned int* counter, double* result) {
+    __shared__ double sh[ND][kThreads / 32];
+    __shared__ bool is_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[k][w];
+            partials[(size_t)blockIdx.x * ND + k] = s;
+        }
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double acc[ND];
+#pragma unroll
+    for (int k = 0; k < ND; k++) acc[k] = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < ND; k++) acc[k] += __ldcg(&partials[(size_t)b * ND + k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+        double s = warp_sum(acc[k]);
+        if (lane == 0) sh[k][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[k][w];
+            result[k] = s;
+        }
+        *counter = 0u;
+    }
+}
+
+// Rounded arithmetic without contraction, so that FP64 epilogues round exactly like the
+// plain C statement of the method.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+
+}  // namespace uaamg

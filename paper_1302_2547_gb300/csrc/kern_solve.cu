@@ -1,0 +1,404 @@
+// kern_solve.cu -- kernels of the solve phase: CSR SpMV fused with the l1-Jacobi smoother
+// (Sections 4.1, 4.4), residual restriction and piecewise-constant prolongation
+// (Section 4.2), the scalar steps of the K-cycle (Section 4.3) and of the outer flexible CG.
+//
+// Row-block SpMV: a block owns 256 consecutive rows.  Their entries form one contiguous
+// range of col/val, which the block streams in chunks with coalesced loads, multiplying
+// each value by the gathered vector entry into shared memory; each thread then adds its
+// own row's products in stored order and applies the fused epilogue.  Loads are therefore
+// coalesced whatever the row lengths, and every row sum has a fixed order.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace uaamg {
+
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+    return __ldcs(p);
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ T rb_gather(const RBArgs<T>& a, int j) {
+    if constexpr (MODE == RB_PRE1) return mul_rn(a.minv[j], a.r[j]);
+    else if constexpr (MODE == RB_PROSMOOTH) return add_rn(a.x[j], a.e[a.agg[j]]);
+    else return a.x[j];
+}
+
+template <typename T, int MODE, int ND>
+__global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
+    if (a.skip && *(volatile const int*)a.skip) return;
+    __shared__ T prod[kChunk];
+    const int r0 = blockIdx.x * kRowsPerBlock;
+    const int r1 = min(a.n, r0 + kRowsPerBlock);
+    const int row = r0 + threadIdx.x;
+    const int k0 = a.rowptr[r0], k1 = a.rowptr[r1];
+    int rs = 0, re = 0;
+    if (row < r1) {
+        rs = a.rowptr[row];
+        re = a.rowptr[row + 1];
+    }
+    T acc = T(0);
+    for (int c0 = k0; c0 < k1; c0 += kChunk) {
+        const int c1 = min(k1, c0 + kChunk);
+#pragma unroll 4
+        for (int k = c0 + threadIdx.x; k < c1; k += kThreads) {
+            const int j = ld_stream(a.col + k);
+            prod[k - c0] = mul_rn(ld_stream(a.val + k), rb_gather<T, MODE>(a, j));
+        }
+        __syncthreads();
+        const int lo = max(rs, c0), hi = min(re, c1);
+        for (int k = lo; k < hi; k++) acc = add_rn(acc, prod[k - c0]);
+        __syncthreads();
+    }
+    double dv[ND > 0 ? ND : 1];
+#pragma unroll
+    for (int k = 0; k < (ND > 0 ? ND : 1); k++) dv[k] = 0.0;
+    if (row < r1) {
+        const int i = row;
+        if constexpr (MODE == RB_PRE1) {
+            a.y[i] = mul_rn(a.minv[i], a.r[i]);
+            a.y2[i] = sub_rn(a.r[i], acc);
+        } else if constexpr (MODE == RB_SMOOTH) {
+            a.y[i] = add_rn(a.x[i], mul_rn(a.minv[i], sub_rn(a.r[i], acc)));
+        } else if constexpr (MODE == RB_RESID) {
+            const T yi = sub_rn(a.r[i], acc);
+            a.y[i] = yi;
+            if constexpr (ND >= 1) dv[0] = (double)yi * (double)yi;
+        } else if constexpr (MODE == RB_PROSMOOTH) {
+            const T xi = add_rn(a.x[i], a.e[a.agg[i]]);
+            a.y[i] = add_rn(xi, mul_rn(a.minv[i], sub_rn(a.r[i], acc)));
+        } else {  // RB_SPMV
+            a.y[i] = acc;
+            const double xi = (double)a.x[i];
+            if constexpr (ND >= 1) dv[0] = xi * (double)acc;
+            if constexpr (ND >= 2) dv[1] = xi * (double)a.d1[i];
+            if constexpr (ND >= 3) dv[2] = xi * (double)a.d2[i];
+        }
+    }
+    if constexpr (ND > 0) grid_reduce<ND>(dv, a.partials, a.counter, a.result);
+}
+
+template <typename T>
+int launch_rowblock(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
+    const int grid = grid_for(a.n, kRowsPerBlock);
+    cudaStream_t st = h->work;
+#define RB_CASE(M, D)                                                 \
+    if (mode == M && ndots == D) {                                    \
+        k_rowblock<T, M, D><<<grid, kThreads, 0, st>>>(a);            \
+        count_launch(h);                                              \
+        return check_cuda(cudaGetLastError());                        \
+    }
+    RB_CASE(RB_PRE1, 0)
+    RB_CASE(RB_SMOOTH, 0)
+    RB_CASE(RB_RESID, 0)
+    RB_CASE(RB_RESID, 1)
+    RB_CASE(RB_PROSMOOTH, 0)
+    RB_CASE(RB_SPMV, 0)
+    RB_CASE(RB_SPMV, 2)
+    RB_CASE(RB_SPMV, 3)
+#undef RB_CASE
+    return UAAMG_ERR_INVALID_ARG;
+}
+
+template int launch_rowblock<float>(Handle*, int, int, const RBArgs<float>&);
+template int launch_rowblock<double>(Handle*, int, int, const RBArgs<double>&);
+
+// ---------------------------------------------------------------------------------------
+// Restriction (Section 4.2): (P^T s)_I = sum of s over the members of aggregate I, one
+// thread per coarse entry, members in ascending order.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_restrict(int nc, const int* __restrict__ aggptr, const int* __restrict__ members,
+           const T* __restrict__ s, T* __restrict__ rc, const int* skip) {
+    if (skip && *(volatile const int*)skip) return;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    T sum = T(0);
+    for (int q = aggptr[I]; q < aggptr[I + 1]; q++) sum = add_rn(sum, s[members[q]]);
+    rc[I] = sum;
+}
+
+template <typename T>
+int launch_restrict(Handle* h, int nc, const int* aggptr, const int* members, const T* s,
+                    T* rc, const int* skip) {
+    k_restrict<T><<<grid_for(nc, kThreads), kThreads, 0, h->work>>>(nc, aggptr, members, s, rc, skip);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+template int launch_restrict<float>(Handle*, int, const int*, const int*, const float*, float*, const int*);
+template int launch_restrict<double>(Handle*, int, const int*, const int*, const double*, double*, const int*);
+
+// ---------------------------------------------------------------------------------------
+// Coarsest solve: out = A_c^{-1} in with the precomputed dense inverse (warp per row, FP64).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_dense_apply(int n, const double* __restrict__ inv, const T* __restrict__ in,
+              T* __restrict__ out, const int* skip) {
+    if (skip && *(volatile const int*)skip) return;
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s += inv[(size_t)i * n + j] * (double)in[j];
+    s = warp_sum(s);
+    if (lane == 0) out[i] = (T)s;
+}
+
+template <typename T>
+int launch_dense_apply(Handle* h, int n, const double* inv, const T* in, T* out,
+                       const int* skip) {
+    k_dense_apply<T><<<grid_for((long long)n * 32, kThreads), kThreads, 0, h->work>>>(n, inv, in, out, skip);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+template int launch_dense_apply<float>(Handle*, int, const double*, const float*, float*, const int*);
+template int launch_dense_apply<double>(Handle*, int, const double*, const double*, double*, const int*);
+
+// ---------------------------------------------------------------------------------------
+// K-cycle scalar steps (Section 4.3, two flexible-CG steps):
+//   step 1: rho~ = rho - (alpha1 / rho1) v1; the second step is skipped when rho1 <= 0,
+//           when only one step is configured, or when |rho~| <= tau |rho| (tau > 0).
+//   combine: e = (alpha1/rho1 - gamma alpha2 / (rho1 rho2)) c1 + (alpha2 / rho2) c2 with
+//           rho2 = beta - gamma^2 / rho1, falling back to (alpha1/rho1) c1 when the second
+//           step was skipped or rho2 <= 0, and to 0 when rho1 <= 0.
+// Ctrl::skip = level+1 while the kernels of a skipped second step must return at once.
+// ---------------------------------------------------------------------------------------
+template <typename T, bool TAU>
+__global__ void __launch_bounds__(kThreads)
+k_kc_rt(int level, int n, const T* __restrict__ rho, const T* __restrict__ v1, T* __restrict__ rt,
+        LevelScalars* sc, int inner, double tau, Ctrl* ctrl, double* partials) {
+    if (*(volatile const int*)&ctrl->skip) return;
+    const double rho1 = sc->rho1, alpha1 = sc->alpha1;
+    const bool ok = rho1 > 0.0;
+    const double a1 = ok ? alpha1 / rho1 : 0.0;
+    const T a1t = (T)a1;
+    double dv[2] = {0.0, 0.0};
+    const int gs = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
+        const T v = sub_rn(rho[i], mul_rn(a1t, v1[i]));
+        rt[i] = v;
+        if constexpr (TAU) {
+            dv[0] += (double)v * (double)v;
+            dv[1] += (double)rho[i] * (double)rho[i];
+        }
+    }
+    if constexpr (TAU) grid_reduce<2>(dv, partials, &ctrl->red_count, &sc->rtrt);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int skip2 = (!ok || inner < 2) ? 1 : 0;
+        sc->skip2 = skip2;
+        if (skip2) ctrl->skip = level + 1;
+    }
+}
+
+// The tau test needs the complete norms, so it runs as its own one-block step.
+__global__ void k_kc_tau(int level, LevelScalars* sc, double tau, Ctrl* ctrl) {
+    if (*(volatile const int*)&ctrl->skip) return;
+    if (threadIdx.x == 0 && !sc->skip2) {
+        if (sqrt(sc->rtrt) <= tau * sqrt(sc->rhorho)) {
+            sc->skip2 = 1;
+            ctrl->skip = level + 1;
+        }
+    }
+}
+
+template <typename T>
+int launch_kc_rt(Handle* h, int level, int n, const T* rho, const T* v1, T* rt,
+                 LevelScalars* sc, int inner, double tau, Ctrl* ctrl) {
+    int grid = grid_for(n, kThreads);
+    if (grid > 4 * h->num_sms) grid = 4 * h->num_sms;
+    if (tau > 0.0 && inner >= 2) {
+        k_kc_rt<T, true><<<grid, kThreads, 0, h->work>>>(level, n, rho, v1, rt, sc, inner, tau, ctrl, h->partials);
+        k_kc_tau<<<1, 32, 0, h->work>>>(level, sc, tau, ctrl);
+        count_launch(h, 2);
+    } else {
+        k_kc_rt<T, false><<<grid, kThreads, 0, h->work>>>(level, n, rho, v1, rt, sc, inner, tau, ctrl, h->partials);
+        count_launch(h);
+    }
+    return check_cuda(cudaGetLastError());
+}
+template int launch_kc_rt<float>(Handle*, int, int, const float*, const float*, float*, LevelScalars*, int, double, Ctrl*);
+template int launch_kc_rt<double>(Handle*, int, int, const double*, const double*, double*, LevelScalars*, int, double, Ctrl*);
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_kc_combine(int level, int n, const T* __restrict__ c1, const T* __restrict__ c2,
+             T* __restrict__ e, const LevelScalars* sc, Ctrl* ctrl) {
+    const int sk = *(volatile const int*)&ctrl->skip;
+    if (sk != 0 && sk != level + 1) return;  // inside an ancestor's skipped step
+    const double rho1 = sc->rho1, alpha1 = sc->alpha1;
+    double w1 = 0.0, w2 = 0.0;
+    if (rho1 > 0.0) {
+        w1 = alpha1 / rho1;
+        if (!sc->skip2) {
+            const double gamma = sc->gamma, beta = sc->beta, alpha2 = sc->alpha2;
+            const double rho2 = beta - gamma * gamma / rho1;
+            if (rho2 > 0.0) {
+                w1 = w1 - gamma * alpha2 / (rho1 * rho2);
+                w2 = alpha2 / rho2;
+            }
+        }
+    }
+    const T w1t = (T)w1, w2t = (T)w2;
+    const bool two = (w2 != 0.0);
+    const int gs = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
+        T v = mul_rn(w1t, c1[i]);
+        if (two) v = add_rn(v, mul_rn(w2t, c2[i]));
+        e[i] = v;
+    }
+    if (sk == level + 1 && blockIdx.x == 0 && threadIdx.x == 0) ctrl->skip = 0;
+}
+
+template <typename T>
+int launch_kc_combine(Handle* h, int level, int n, const T* c1, const T* c2, T* e,
+                      const LevelScalars* sc, Ctrl* ctrl) {
+    int grid = grid_for(n, kThreads);
+    if (grid > 8 * h->num_sms) grid = 8 * h->num_sms;
+    k_kc_combine<T><<<grid, kThreads, 0, h->work>>>(level, n, c1, c2, e, sc, ctrl);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+template int launch_kc_combine<float>(Handle*, int, int, const float*, const float*, float*, const LevelScalars*, Ctrl*);
+template int launch_kc_combine<double>(Handle*, int, int, const double*, const double*, double*, const LevelScalars*, Ctrl*);
+
+// Prolongation alone (Section 4.2): y_i = x_i + e_{agg[i]} (x = null: zero).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_prolong(int n, const T* __restrict__ x, const int* __restrict__ agg, const T* __restrict__ e,
+          T* __restrict__ y, const int* skip) {
+    if (skip && *(volatile const int*)skip) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = x ? add_rn(x[i], e[agg[i]]) : e[agg[i]];
+}
+
+template <typename T>
+int launch_prolong(Handle* h, int n, const T* x, const int* agg, const T* e, T* y,
+                   const int* skip) {
+    k_prolong<T><<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, x, agg, e, y, skip);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+template int launch_prolong<float>(Handle*, int, const float*, const int*, const float*, float*, const int*);
+template int launch_prolong<double>(Handle*, int, const double*, const int*, const double*, double*, const int*);
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_copy(int n, const T* __restrict__ in, T* __restrict__ out, const int* skip) {
+    if (skip && *(volatile const int*)skip) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in ? in[i] : T(0);
+}
+
+template <typename T>
+int launch_copy(Handle* h, int n, const T* in, T* out, const int* skip) {
+    k_copy<T><<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, in, out, skip);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+template int launch_copy<float>(Handle*, int, const float*, float*, const int*);
+template int launch_copy<double>(Handle*, int, const double*, double*, const int*);
+
+// ---------------------------------------------------------------------------------------
+// Outer flexible CG (FP64): p = z - ((z, q_prev) / (p_prev, q_prev)) p_prev, q = A p,
+// alpha = (p, r) / (p, q), x += alpha p, r -= alpha q.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_cast_d2f(int n, const double* __restrict__ in, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __double2float_rn(in[i]);
+}
+
+int launch_cast_d2f(Handle* h, int n, const double* in, float* out) {
+    k_cast_d2f<<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, in, out);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(kThreads)
+k_dot(int n, const TA* __restrict__ a, const TB* __restrict__ b, double* partials,
+      unsigned int* counter, double* result) {
+    double dv[1] = {0.0};
+    const int gs = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs)
+        dv[0] += (double)a[i] * (double)b[i];
+    grid_reduce<1>(dv, partials, counter, result);
+}
+
+static int dot_grid(Handle* h, int n) {
+    int g = grid_for(n, kThreads);
+    return g > 4 * h->num_sms ? 4 * h->num_sms : g;
+}
+
+int launch_dot(Handle* h, int n, const double* a, const double* b, double* result) {
+    k_dot<double, double><<<dot_grid(h, n), kThreads, 0, h->work>>>(n, a, b, h->partials, &h->ctrl->red_count, result);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+
+template <typename T>
+int launch_outer_zq(Handle* h, int n, const T* z, const double* q, OuterScalars* osc) {
+    k_dot<T, double><<<dot_grid(h, n), kThreads, 0, h->work>>>(n, z, q, h->partials, &h->ctrl->red_count, &osc->zq);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+template int launch_outer_zq<float>(Handle*, int, const float*, const double*, OuterScalars*);
+template int launch_outer_zq<double>(Handle*, int, const double*, const double*, OuterScalars*);
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_outer_p(int n, const T* __restrict__ z, double* __restrict__ p, const OuterScalars* osc) {
+    const double beta = osc->first ? 0.0 : osc->zq / osc->pq_prev;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = __dsub_rn((double)z[i], __dmul_rn(beta, p[i]));
+}
+
+template <typename T>
+int launch_outer_p(Handle* h, int n, const T* z, double* p, OuterScalars* osc) {
+    k_outer_p<T><<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, z, p, osc);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+template int launch_outer_p<float>(Handle*, int, const float*, double*, OuterScalars*);
+template int launch_outer_p<double>(Handle*, int, const double*, double*, OuterScalars*);
+
+__global__ void __launch_bounds__(kThreads)
+k_outer_xr(int n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+           const double* __restrict__ q, OuterScalars* osc, double* partials,
+           unsigned int* counter) {
+    const double pq = osc->pq;
+    const bool ok = pq > 0.0;
+    const double alpha = ok ? osc->pr / pq : 0.0;
+    double dv[1] = {0.0};
+    const int gs = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
+        x[i] = __dadd_rn(x[i], __dmul_rn(alpha, p[i]));
+        const double ri = __dsub_rn(r[i], __dmul_rn(alpha, q[i]));
+        r[i] = ri;
+        dv[0] += ri * ri;
+    }
+    grid_reduce<1>(dv, partials, counter, &osc->rr);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // fields read only by the next iteration's kernels
+        osc->alpha = alpha;
+        osc->pq_prev = pq;
+        osc->first = 0;
+        if (!ok) osc->breakdown = 1;
+    }
+}
+
+int launch_outer_xr(Handle* h, int n, double* x, double* r, const double* p, const double* q,
+                    OuterScalars* osc) {
+    k_outer_xr<<<dot_grid(h, n), kThreads, 0, h->work>>>(n, x, r, p, q, osc, h->partials, &h->ctrl->red_count);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_to_host_scalars(Handle* h) {
+    return check_cuda(cudaMemcpyAsync(h->osc_host, h->osc, sizeof(OuterScalars),
+                                      cudaMemcpyDeviceToHost, h->work));
+}
+
+}  // namespace uaamg

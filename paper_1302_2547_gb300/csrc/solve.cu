@@ -1,0 +1,414 @@
+// solve.cu -- host driver of the solve phase: the multigrid preconditioner B_l
+// (Algorithm 1, solve phase), the K-cycle K_m (Section 4.3: two flexible-CG steps per coarse
+// level) and the outer flexible CG (Sections 1 and 4.4).  All scalars stay on the device;
+// the host issues kernels in a fixed order, so one outer iteration is captured once as a
+// CUDA graph and replayed.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace uaamg {
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<float> {
+    static const float* val(const Level& L) { return L.val32; }
+    static const float* minv(const Level& L) { return L.minv32; }
+};
+template <>
+struct Prec<double> {
+    static const double* val(const Level& L) { return L.val64; }
+    static const double* minv(const Level& L) { return L.minv64; }
+};
+
+// ---- profiling: events around level-0 launches of the selected kernel class ----------------
+static int prof_begin(Handle* h, int cls, int level) {
+    if (h->prof_class != cls || level != 0) return -1;
+    ProfSlot ps{};
+    cudaEventCreate(&ps.a);
+    cudaEventCreate(&ps.b);
+    if (h->capturing) cudaEventRecordWithFlags(ps.a, h->work, cudaEventRecordExternal);
+    else cudaEventRecord(ps.a, h->work);
+    h->prof_slots.push_back(ps);
+    return (int)h->prof_slots.size() - 1;
+}
+static void prof_end(Handle* h, int slot) {
+    if (slot < 0) return;
+    if (h->capturing) cudaEventRecordWithFlags(h->prof_slots[slot].b, h->work, cudaEventRecordExternal);
+    else cudaEventRecord(h->prof_slots[slot].b, h->work);
+}
+
+// Algorithmic bytes of one launch of a profiled kernel class (matrix once, vectors once).
+static double class_bytes(const Handle* h, int cls) {
+    const Level& L = h->lev[0];
+    const double n = L.n, z = (double)L.nnz;
+    const double f = (h->p.precision == UAAMG_MIXED) ? 4.0 : 8.0;
+    if (cls == UAAMG_KCLASS_SMOOTH0) {
+        // pre-smoother + residual: z(f+4) + 4(n+1) + r, Minv read + x, s written (4 n f);
+        // prolongation + post-smoother: z(f+4) + 4(n+1) + x, r, Minv, y (4 n f) + agg + e_c
+        const double pre = z * (f + 4) + 4 * (n + 1) + 4 * n * f;
+        const double post = z * (f + 4) + 4 * (n + 1) + 4 * n * f + 4 * n + (double)L.nc * f;
+        return 0.5 * (pre + post);
+    }
+    if (cls == UAAMG_KCLASS_SPMV64) return z * 12.0 + 4 * (n + 1) + 3 * n * 8.0;
+    return 0.0;
+}
+
+template <typename T>
+static RBArgs<T> rb_args(Handle* h, const Level& L) {
+    RBArgs<T> a{};
+    a.n = L.n;
+    a.rowptr = L.rowptr;
+    a.col = L.col;
+    a.val = Prec<T>::val(L);
+    a.minv = Prec<T>::minv(L);
+    a.partials = h->partials;
+    a.counter = &h->ctrl->red_count;
+    a.skip = &h->ctrl->skip;
+    return a;
+}
+
+template <typename T>
+static int apply_K(Handle* h, int m, const T* in, T* out);
+
+// out = B_l(in): `pre` l1-Jacobi sweeps from zero, residual restriction, coarse correction
+// by K_{l+1}, prolongation, `post` sweeps.  On the coarsest level, the exact solve.
+template <typename T>
+static int apply_B(Handle* h, int l, const T* in, T* out) {
+    const int* skip = &h->ctrl->skip;
+    if (l == h->nlev - 1) return launch_dense_apply<T>(h, h->nco, h->coarse_inv, in, out, skip);
+    Level& L = h->lev[l];
+    Level& C = h->lev[l + 1];
+    T* w = (T*)L.w;
+    T* s = (T*)L.s;
+    T* rc = (T*)C.rhs;
+    T* ec = (T*)C.out;
+    const int pre = h->p.pre, post = h->p.post;
+    const int nwrites = pre + (post >= 1 ? post : 1);
+    int k = 0;
+    auto buf = [&](int idx) -> T* { return ((nwrites - 1 - idx) % 2 == 0) ? out : w; };
+    const T* x = nullptr;
+    int st;
+    if (pre >= 1) {
+        RBArgs<T> a = rb_args<T>(h, L);
+        a.r = in;
+        T* y = buf(k++);
+        a.y = y;
+        a.y2 = s;
+        int ps = prof_begin(h, UAAMG_KCLASS_SMOOTH0, l);
+        if ((st = launch_rowblock<T>(h, RB_PRE1, 0, a))) return st;
+        prof_end(h, ps);
+        x = y;
+        for (int i = 1; i < pre; i++) {
+            RBArgs<T> b = rb_args<T>(h, L);
+            b.r = in;
+            b.x = x;
+            T* y2 = buf(k++);
+            b.y = y2;
+            if ((st = launch_rowblock<T>(h, RB_SMOOTH, 0, b))) return st;
+            x = y2;
+        }
+        if (pre >= 2) {
+            RBArgs<T> c = rb_args<T>(h, L);
+            c.r = in;
+            c.x = x;
+            c.y = s;
+            if ((st = launch_rowblock<T>(h, RB_RESID, 0, c))) return st;
+        }
+        if ((st = launch_restrict<T>(h, L.nc, L.aggptr, L.members, s, rc, skip))) return st;
+    } else {
+        if ((st = launch_restrict<T>(h, L.nc, L.aggptr, L.members, in, rc, skip))) return st;
+        if ((st = launch_copy<T>(h, L.n, nullptr, s, skip))) return st;  // x = 0
+        x = s;
+    }
+    if ((st = apply_K<T>(h, l + 1, rc, ec))) return st;
+    {
+        RBArgs<T> a = rb_args<T>(h, L);
+        a.r = in;
+        a.x = x;
+        a.agg = L.agg;
+        a.e = ec;
+        T* y = buf(k++);
+        a.y = y;
+        if (post >= 1) {
+            int ps = prof_begin(h, UAAMG_KCLASS_SMOOTH0, l);
+            if ((st = launch_rowblock<T>(h, RB_PROSMOOTH, 0, a))) return st;
+            prof_end(h, ps);
+        } else {
+            if ((st = launch_prolong<T>(h, L.n, x, L.agg, ec, y, skip))) return st;
+        }
+        x = y;
+        for (int i = 1; i < post; i++) {
+            RBArgs<T> b = rb_args<T>(h, L);
+            b.r = in;
+            b.x = x;
+            T* y2 = buf(k++);
+            b.y = y2;
+            if ((st = launch_rowblock<T>(h, RB_SMOOTH, 0, b))) return st;
+            x = y2;
+        }
+    }
+    return UAAMG_OK;
+}
+
+// out = K_m(in) for m >= 1: two flexible-CG steps on A_m e = in preconditioned by B_m
+// (exact solve on the coarsest level).
+template <typename T>
+static int apply_K(Handle* h, int m, const T* in, T* out) {
+    const int* skip = &h->ctrl->skip;
+    if (m == h->nlev - 1) return launch_dense_apply<T>(h, h->nco, h->coarse_inv, in, out, skip);
+    Level& L = h->lev[m];
+    T *c1 = (T*)L.c1, *v1 = (T*)L.v1, *rt = (T*)L.rt, *c2 = (T*)L.c2, *v2 = (T*)L.v2;
+    int st;
+    if ((st = apply_B<T>(h, m, in, c1))) return st;
+    {
+        RBArgs<T> a = rb_args<T>(h, L);
+        a.x = c1;
+        a.y = v1;
+        a.d1 = in;
+        a.result = &L.sc->rho1;  // (c1, A c1), (c1, rho)
+        if ((st = launch_rowblock<T>(h, RB_SPMV, 2, a))) return st;
+    }
+    const int inner = h->p.kcycle_inner;
+    if ((st = launch_kc_rt<T>(h, m, L.n, in, v1, rt, L.sc, inner, h->p.kcycle_tau, h->ctrl)))
+        return st;
+    if (inner >= 2) {
+        if ((st = apply_B<T>(h, m, rt, c2))) return st;
+        RBArgs<T> a = rb_args<T>(h, L);
+        a.x = c2;
+        a.y = v2;
+        a.d1 = v1;
+        a.d2 = rt;
+        a.result = &L.sc->beta;  // (c2, A c2), (c2, v1), (c2, rho~)
+        if ((st = launch_rowblock<T>(h, RB_SPMV, 3, a))) return st;
+    }
+    return launch_kc_combine<T>(h, m, L.n, c1, c2, out, L.sc, h->ctrl);
+}
+
+// One outer flexible-CG iteration (everything on the device).
+template <typename T>
+static int outer_iteration(Handle* h) {
+    Level& L0 = h->lev[0];
+    const int n = L0.n;
+    int st;
+    const T* rin;
+    if constexpr (sizeof(T) == 4) {
+        if ((st = launch_cast_d2f(h, n, h->r, (float*)L0.rhs))) return st;
+        rin = (const T*)L0.rhs;
+    } else {
+        rin = (const T*)h->r;
+    }
+    T* z = (T*)L0.out;
+    if ((st = apply_B<T>(h, 0, rin, z))) return st;
+    if ((st = launch_outer_zq<T>(h, n, z, h->q, h->osc))) return st;
+    if ((st = launch_outer_p<T>(h, n, z, h->p_, h->osc))) return st;
+    {
+        RBArgs<double> a{};
+        a.n = n;
+        a.rowptr = L0.rowptr;
+        a.col = L0.col;
+        a.val = L0.val64;
+        a.x = h->p_;
+        a.y = h->q;
+        a.d1 = h->r;
+        a.partials = h->partials;
+        a.counter = &h->ctrl->red_count;
+        a.result = &h->osc->pq;  // (p, A p), (p, r)
+        int ps = prof_begin(h, UAAMG_KCLASS_SPMV64, 0);
+        if ((st = launch_rowblock<double>(h, RB_SPMV, 2, a))) return st;
+        prof_end(h, ps);
+    }
+    if ((st = launch_outer_xr(h, n, h->x, h->r, h->p_, h->q, h->osc))) return st;
+    return launch_to_host_scalars(h);
+}
+
+static int run_iteration(Handle* h) {
+    if (h->p.precision == UAAMG_MIXED) return outer_iteration<float>(h);
+    return outer_iteration<double>(h);
+}
+
+static int ensure_graph(Handle* h) {
+    if (h->graph || !h->p.use_graphs) return UAAMG_OK;
+    cudaGraph_t g = nullptr;
+    h->capturing = true;
+    h->graph_nodes = 0;
+    size_t slot0 = h->prof_slots.size();
+    int st = check_cuda(cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal));
+    if (st == UAAMG_OK) {
+        int st2 = run_iteration(h);
+        st = check_cuda(cudaStreamEndCapture(h->work, &g));
+        if (st2) st = st2;
+    }
+    h->capturing = false;
+    if (st == UAAMG_OK) st = check_cuda(cudaGraphInstantiate(&h->graph, g, 0));
+    if (g) cudaGraphDestroy(g);
+    if (st != UAAMG_OK) {
+        h->graph = nullptr;
+        h->prof_slots.resize(slot0);
+        cudaGetLastError();
+    }
+    return st;
+}
+
+static void harvest_profile(Handle* h) {
+    for (auto& ps : h->prof_slots) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ps.a, ps.b) == cudaSuccess) {
+            h->prof_ms += ms;
+            h->prof_launches++;
+        }
+    }
+    cudaGetLastError();
+}
+
+// Host-side readback of the scalars after an iteration (the copy is part of the iteration).
+static int iterate_once(Handle* h) {
+    int st;
+    if (h->graph) {
+        st = check_cuda(cudaGraphLaunch(h->graph, h->work));
+        count_launch(h, h->graph_nodes);
+    } else {
+        size_t s0 = h->prof_slots.size();
+        st = run_iteration(h);
+        if (st == UAAMG_OK) st = check_cuda(cudaStreamSynchronize(h->work));
+        if (st == UAAMG_OK && h->prof_class) {
+            for (size_t i = s0; i < h->prof_slots.size(); i++) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, h->prof_slots[i].a, h->prof_slots[i].b) == cudaSuccess) {
+                    h->prof_ms += ms;
+                    h->prof_launches++;
+                }
+                cudaEventDestroy(h->prof_slots[i].a);
+                cudaEventDestroy(h->prof_slots[i].b);
+            }
+            h->prof_slots.resize(s0);
+        }
+        return st;
+    }
+    if (st == UAAMG_OK) st = check_cuda(cudaStreamSynchronize(h->work));
+    if (st == UAAMG_OK && h->prof_class) harvest_profile(h);
+    return st;
+}
+
+static int true_residual(Handle* h) {
+    Level& L0 = h->lev[0];
+    RBArgs<double> a{};
+    a.n = L0.n;
+    a.rowptr = L0.rowptr;
+    a.col = L0.col;
+    a.val = L0.val64;
+    a.x = h->x;
+    a.r = h->b;
+    a.y = h->r;
+    a.partials = h->partials;
+    a.counter = &h->ctrl->red_count;
+    a.result = &h->osc->rr;
+    int st = launch_rowblock<double>(h, RB_RESID, 1, a);
+    if (st) return st;
+    if ((st = launch_to_host_scalars(h))) return st;
+    return check_cuda(cudaStreamSynchronize(h->work));
+}
+
+int solve(Handle* h, const double* b, double* x, double tol, int use_guess, int* iters,
+          double* relres) {
+    Level& L0 = h->lev[0];
+    const int n = L0.n;
+    int st;
+    *iters = 0;
+    *relres = 0.0;
+    h->hist.clear();
+    cudaEventRecord(h->ev_t0, h->work);
+    if ((st = check_cuda(cudaMemcpyAsync(h->b, b, sizeof(double) * n, cudaMemcpyDefault, h->work))))
+        return st;
+    if (use_guess)
+        st = check_cuda(cudaMemcpyAsync(h->x, x, sizeof(double) * n, cudaMemcpyDefault, h->work));
+    else
+        st = check_cuda(cudaMemsetAsync(h->x, 0, sizeof(double) * n, h->work));
+    if (st) return st;
+    OuterScalars init{};
+    init.first = 1;
+    *h->osc_host = init;
+    cudaMemcpyAsync(h->osc, h->osc_host, sizeof(OuterScalars), cudaMemcpyHostToDevice, h->work);
+    cudaMemsetAsync(h->p_, 0, sizeof(double) * n, h->work);
+    cudaMemsetAsync(h->q, 0, sizeof(double) * n, h->work);
+    cudaMemsetAsync(&h->ctrl->skip, 0, sizeof(int), h->work);
+    if ((st = launch_dot(h, n, h->b, h->b, &h->osc->bb))) return st;
+    if ((st = true_residual(h))) return st;  // r = b - A x, rr
+    double bn = sqrt(h->osc_host->bb);
+    double rn = sqrt(h->osc_host->rr);
+    int status = UAAMG_ERR_NO_CONVERGENCE;
+    if (bn == 0.0) {
+        cudaMemsetAsync(h->x, 0, sizeof(double) * n, h->work);
+        rn = 0.0;
+        bn = 1.0;
+    }
+    h->hist.push_back(rn / bn);
+    if (rn <= tol * bn) status = UAAMG_OK;
+    if (status != UAAMG_OK && (st = ensure_graph(h))) return st;
+    int k = 0;
+    while (status != UAAMG_OK && k < h->p.max_iter) {
+        if ((st = iterate_once(h))) return st;
+        k++;
+        if (h->osc_host->breakdown) break;
+        rn = sqrt(h->osc_host->rr);
+        if (rn <= tol * bn) {
+            if ((st = true_residual(h))) return st;
+            rn = sqrt(h->osc_host->rr);
+            if (rn <= tol * bn) status = UAAMG_OK;
+        }
+        h->hist.push_back(rn / bn);
+    }
+    if ((st = check_cuda(cudaMemcpyAsync(x, h->x, sizeof(double) * n, cudaMemcpyDefault, h->work))))
+        return st;
+    cudaEventRecord(h->ev_t1, h->work);
+    if ((st = check_cuda(cudaStreamSynchronize(h->work)))) return st;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1);
+    h->solve_ms = ms;
+    *iters = k;
+    *relres = rn / bn;
+    return status;
+}
+
+// Host-vector wrappers of B_l and K_m for the parity tests.
+template <typename T>
+static int apply_host(Handle* h, int which, int l, const double* in, double* out) {
+    const Level& L = h->lev[l];
+    const int n = L.n;
+    int st = UAAMG_OK;
+    double* d = nullptr;
+    if ((st = check_cuda(cudaMalloc(&d, sizeof(double) * n * 2)))) return st;
+    T* tin = (T*)L.rhs;
+    T* tout = (T*)L.out;
+    T* tmp_in = nullptr;
+    if (l == 0 && sizeof(T) == 8) tin = (T*)(d + n);  // level-0 rhs aliases the outer residual
+    cudaMemcpyAsync(d, in, sizeof(double) * n, cudaMemcpyHostToDevice, h->work);
+    cudaMemsetAsync(&h->ctrl->skip, 0, sizeof(int), h->work);
+    if constexpr (sizeof(T) == 4) {
+        launch_cast_d2f(h, n, d, (float*)tin);
+    } else {
+        cudaMemcpyAsync(tin, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->work);
+    }
+    (void)tmp_in;
+    if (which == 0) st = apply_B<T>(h, l, tin, tout);
+    else st = apply_K<T>(h, l, tin, tout);
+    if (st == UAAMG_OK) {
+        std::vector<T> host(n);
+        cudaMemcpyAsync(host.data(), tout, sizeof(T) * n, cudaMemcpyDeviceToHost, h->work);
+        st = check_cuda(cudaStreamSynchronize(h->work));
+        for (int i = 0; i < n; i++) out[i] = (double)host[i];
+    }
+    cudaFree(d);
+    return st;
+}
+
+int apply_operator(Handle* h, int which, int l, const double* in, double* out) {
+    if (h->p.precision == UAAMG_MIXED) return apply_host<float>(h, which, l, in, out);
+    return apply_host<double>(h, which, l, in, out);
+}
+
+double profile_bytes(const Handle* h) { return class_bytes(h, h->prof_class); }
+
+}  // namespace uaamg

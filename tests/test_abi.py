@@ -1,0 +1,90 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads, exports every symbol that
+include/uaamg.h declares, and refuses to compute without a GPU (no CPU fallback)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1302_2547_gb300 import build as B
+
+    return B.build()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "uaamg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(uaamg_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("uaamg_setup", "uaamg_solve", "uaamg_free"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (uaamg_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    from paper_1302_2547_gb300 import _lib as U
+
+    assert set(U.EXPORTS) == set(_declared())
+    L = ctypes.CDLL(built)
+    for n in _declared():
+        getattr(L, n)
+
+
+def test_default_params_and_status_strings(built):
+    from paper_1302_2547_gb300 import _lib as U
+
+    p = U.uaamg_default_params()
+    assert (p.coarse_size, p.max_levels, p.max_agg_size, p.pass_mode) == (64, 25, 5, 1)
+    assert (p.pre, p.post, p.kcycle_inner, p.precision, p.max_iter) == (1, 1, 2, 1, 200)
+    assert U.status_string(0) == "ok" and "CSR" in U.status_string(2)
+
+
+def test_params_are_checked_before_any_device_work(built):
+    from paper_1302_2547_gb300 import _lib as U
+    from paper_1302_2547_gb300 import inputs as I
+
+    A = I.grid2d(8)
+    for bad in ({"max_agg_size": 1}, {"kcycle_inner": 3}, {"precision": 7},
+                {"max_levels": 0}, {"pass_mode": 4}, {"pre": -1}):
+        with pytest.raises(U.UaamgError) as e:
+            U.uaamg_setup(A.rowptr, A.col, A.val, U.uaamg_default_params(**bad))
+        assert e.value.status == 1
+
+
+def test_no_cpu_fallback_without_a_gpu(built):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1302_2547_gb300 import _lib as U
+    from paper_1302_2547_gb300 import inputs as I
+
+    A = I.grid2d(8)
+    with pytest.raises(U.UaamgError) as e:
+        U.uaamg_setup(A.rowptr, A.col, A.val)
+    assert e.value.status == 7  # UAAMG_ERR_CUDA
+
+
+def test_product_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1302_2547_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                for pat in (r"^\s*(from|import)\s+oracle\b", r"liboracle", r"oracle/",
+                            r"uaamg_oracle"):
+                    assert not re.search(pat, text, flags=re.M), (f, pat)

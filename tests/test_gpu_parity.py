@@ -1,0 +1,305 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the same seeded
+inputs.
+
+Bars (stated per test):
+  * priorities, aggregation passes, aggregates, coarse numbering: bit-exact;
+  * coarse matrices and the l1-Jacobi diagonal: bit-exact for every weight (both sides add
+    the same terms in the same order, Eq. 2.4 / Section 4.1);
+  * the two-level operator B (no inner products): FP64 relative 1e-12;
+  * K-cycle and solves: both reach the stated relative residual, the FP64 path within +-1
+    iteration of the oracle, and |A (x_gpu - x_oracle)| <= 2 tol |b| (implied by both
+    residuals, checked on the host in FP64).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_1302_2547_gb300 import _lib as U
+from paper_1302_2547_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("the GPU tests need a CUDA device")
+    from paper_1302_2547_gb300 import build as B
+
+    B.build()
+
+
+OR_KEYS = ("coarse_size", "max_levels", "max_agg_size", "pass_mode", "seed", "pre", "post",
+           "kcycle_inner", "kcycle_tau", "max_iter")
+
+
+def both(A, oracle, **kw):
+    p = U.uaamg_default_params(**kw)
+    h = U.uaamg_setup(A.rowptr, A.col, A.val, p)
+    H = oracle.Hierarchy(A.rowptr, A.col, A.val,
+                         oracle.Params(**{k: getattr(p, k) for k in OR_KEYS}))
+    return h, H, p
+
+
+def bits(a):
+    return np.ascontiguousarray(a, dtype=np.float64).view(np.uint64)
+
+
+def compare_hierarchy(h, H, oracle, seed):
+    nlev = U.uaamg_num_levels(h)
+    assert nlev == H.num_levels
+    for l in range(nlev):
+        n, z, passes = U.uaamg_level_info(h, l)
+        assert (n, z) == (H.n(l), H.nnz(l)), l
+        rp, cc, vv = U.uaamg_get_level_csr(h, l)
+        orp, occ, ovv = H.csr(l)
+        assert np.array_equal(rp, orp) and np.array_equal(cc, occ), l
+        assert np.array_equal(bits(vv), bits(ovv)), l
+        assert np.array_equal(bits(U.uaamg_get_minv(h, l)), bits(H.minv(l))), l
+        if l < nlev - 1:
+            assert passes == H.passes(l), l
+            assert np.array_equal(U.uaamg_get_priorities(h, l),
+                                  oracle.priorities(rp, cc, seed, level=l)), l
+            assert np.array_equal(U.uaamg_get_pass_of(h, l), H.pass_of(l)), l
+            assert np.array_equal(U.uaamg_get_aggregates(h, l), H.agg(l)), l
+
+
+SETUP_CASES = [
+    ("poisson2d_64", lambda: I.poisson2d_64(), {}),
+    ("grid2d_128_t2", lambda: I.grid2d(128), {"max_agg_size": 2}),
+    ("grid2d_131_maximal", lambda: I.grid2d(131, 77), {"pass_mode": 0, "max_agg_size": 0}),
+    ("grid3d_21_lognormal", lambda: I.grid3d(21, 19, 23, sigma=0.25, seed=4), {"max_agg_size": 0}),
+    ("rgg_20k", lambda: I.rgg(20000, 8.0, seed=7), {"max_agg_size": 0}),
+    ("rgg_20k_maximal_t5", lambda: I.rgg(20000, 8.0, seed=7), {"pass_mode": 0}),
+    ("random_int", lambda: I.random_graph(3000, 6000, seed=1), {"max_agg_size": 3}),
+    ("random_real", lambda: I.random_graph(2500, 9000, seed=2, integer_weights=False), {"max_agg_size": 0}),
+    ("path_1000", lambda: I.path_graph(1000, dirichlet=True), {}),
+]
+
+
+@pytest.mark.parametrize("name,make,kw", SETUP_CASES, ids=[c[0] for c in SETUP_CASES])
+def test_setup_parity(oracle, name, make, kw):
+    A = make()
+    h, H, p = both(A, oracle, precision=U.UAAMG_FP64, **kw)
+    try:
+        compare_hierarchy(h, H, oracle, p.seed)
+    finally:
+        U.uaamg_free(h)
+
+
+def test_long_rows_cross_chunks(oracle):
+    """A hub row longer than the shared-memory chunk (2048 entries) and tiny rows."""
+    n = 3500
+    hub = np.zeros(n - 1, dtype=np.int64)
+    leaves = np.arange(1, n)
+    extra_i = np.arange(1, n - 1, 2)
+    ei = np.concatenate([hub, extra_i])
+    ej = np.concatenate([leaves, extra_i + 1])
+    w = np.random.default_rng(3).integers(1, 4, len(ei)).astype(float)
+    wD = np.zeros(n)
+    wD[5] = 1.0
+    A = I.laplacian_from_edges(n, ei, ej, w, wD)
+    h, H, p = both(A, oracle, precision=U.UAAMG_FP64, max_agg_size=0)
+    try:
+        compare_hierarchy(h, H, oracle, p.seed)
+        b = I.rhs_uniform(n, 5)
+        x = np.zeros(n)
+        st, it, rr = U.uaamg_solve(h, b, x, 1e-10)
+        assert st == 0 and rr <= 1e-10
+        Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+        assert np.linalg.norm(b - Asp @ x) <= 1e-10 * np.linalg.norm(b) * 1.0001
+    finally:
+        U.uaamg_free(h)
+
+
+def test_two_level_operator_fp64(oracle):
+    A = I.grid2d(40, 37)
+    for pre, post in ((1, 1), (2, 2), (0, 1), (1, 0), (3, 2)):
+        h, H, _ = both(A, oracle, precision=U.UAAMG_FP64, max_levels=2, coarse_size=2000,
+                       pre=pre, post=post)
+        try:
+            r = np.random.default_rng(pre * 7 + post).standard_normal(A.n)
+            g = U.uaamg_apply_B(h, 0, r)
+            o = H.apply_B(0, r)
+            assert np.linalg.norm(g - o) <= 1e-12 * np.linalg.norm(o), (pre, post)
+        finally:
+            U.uaamg_free(h)
+
+
+@pytest.mark.parametrize("precision", [U.UAAMG_FP64, U.UAAMG_MIXED])
+def test_kcycle_operator(oracle, precision):
+    A = I.grid2d(60)
+    h, H, _ = both(A, oracle, precision=precision)
+    try:
+        assert U.uaamg_num_levels(h) >= 3
+        rho = np.random.default_rng(1).standard_normal(H.n(1))
+        g, o = U.uaamg_apply_K(h, 1, rho), H.apply_K(1, rho)
+        tol = 1e-10 if precision == U.UAAMG_FP64 else 2e-5
+        assert np.linalg.norm(g - o) <= tol * np.linalg.norm(o)
+        r = np.random.default_rng(2).standard_normal(A.n)
+        g, o = U.uaamg_apply_B(h, 0, r), H.apply_B(0, r)
+        assert np.linalg.norm(g - o) <= tol * np.linalg.norm(o)
+    finally:
+        U.uaamg_free(h)
+
+
+SOLVE_CASES = [
+    ("poisson2d_64", lambda: I.poisson2d_64(), {}),
+    ("grid3d_32", lambda: I.grid3d(32, sigma=0.25, seed=1), {"max_agg_size": 0}),
+    ("rgg_30k", lambda: I.rgg(30000, 8.0, seed=2), {"max_agg_size": 0}),
+    ("random_real", lambda: I.random_graph(4000, 12000, seed=9, integer_weights=False), {"max_agg_size": 0}),
+    ("grid2d_100_tau", lambda: I.grid2d(100), {"kcycle_tau": 0.25}),
+    ("grid2d_100_inner1", lambda: I.grid2d(100), {"kcycle_inner": 1}),
+    ("grid2d_90_pre2post2", lambda: I.grid2d(90, 70), {"pre": 2, "post": 2}),
+]
+
+
+@pytest.mark.parametrize("precision", [U.UAAMG_FP64, U.UAAMG_MIXED])
+@pytest.mark.parametrize("name,make,kw", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_solve_parity(oracle, name, make, kw, precision, graphs):
+    A = make()
+    tol = 1e-8
+    h, H, _ = both(A, oracle, precision=precision, use_graphs=graphs, **kw)
+    try:
+        b = I.rhs_uniform(A.n, 2000)
+        x = np.zeros(A.n)
+        st, it, rr = U.uaamg_solve(h, b, x, tol)
+        xo, ito, rro, sto, histo = H.solve(b, tol)
+        assert st == 0 and sto == 0
+        Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+        bn = np.linalg.norm(b)
+        assert np.linalg.norm(b - Asp @ x) <= tol * bn * 1.0001
+        assert np.linalg.norm(Asp @ (x - xo)) <= 2.0001 * tol * bn
+        hist = U.uaamg_residual_history(h)
+        assert len(hist) == it + 1 and abs(hist[-1] - rr) <= 1e-12
+        if precision == U.UAAMG_FP64:
+            assert abs(it - ito) <= 1, (it, ito)
+            k = min(5, len(hist), len(histo))
+            assert np.allclose(hist[:k], histo[:k], rtol=1e-6, atol=0)
+        else:
+            assert it <= ito + 5, (it, ito)
+    finally:
+        U.uaamg_free(h)
+
+
+def test_solve_edge_cases(oracle):
+    # one unknown
+    A = I.laplacian_from_edges(1, [], [], [], [2.0])
+    h = U.uaamg_setup(A.rowptr, A.col, A.val)
+    try:
+        x = np.zeros(1)
+        st, it, rr = U.uaamg_solve(h, np.array([3.0]), x, 1e-12)
+        assert st == 0 and abs(x[0] - 1.5) < 1e-12 and it == 1
+        assert U.uaamg_num_levels(h) == 1
+    finally:
+        U.uaamg_free(h)
+    # a single level (n <= coarse_size): exact in one iteration
+    A = I.grid2d(7)
+    h = U.uaamg_setup(A.rowptr, A.col, A.val, U.uaamg_default_params(precision=U.UAAMG_FP64))
+    try:
+        b = I.rhs_uniform(A.n, 3)
+        x = np.zeros(A.n)
+        st, it, rr = U.uaamg_solve(h, b, x, 1e-12)
+        assert st == 0 and it == 1 and rr < 1e-12
+    finally:
+        U.uaamg_free(h)
+    # zero right-hand side, exact initial guess, non-convergence report
+    A = I.grid2d(50)
+    h = U.uaamg_setup(A.rowptr, A.col, A.val, U.uaamg_default_params(max_iter=2))
+    try:
+        x = np.ones(A.n)
+        st, it, rr = U.uaamg_solve(h, np.zeros(A.n), x, 1e-8)
+        assert st == 0 and it == 0 and np.all(x == 0)
+        b = I.rhs_uniform(A.n, 4)
+        xs = np.linalg.solve(A.dense(), b)
+        x = xs.copy()
+        st, it, rr = U.uaamg_solve(h, b, x, 1e-8, use_guess=True)
+        assert st == 0 and it == 0
+        x = np.zeros(A.n)
+        st, it, rr = U.uaamg_solve(h, b, x, 1e-14)
+        assert st == U.UAAMG_ERR_NO_CONVERGENCE and it == 2 and 0 < rr < 1
+    finally:
+        U.uaamg_free(h)
+
+
+def test_bad_csr_is_rejected():
+    A = I.grid2d(12)
+    cases = []
+    c = A.col.copy()
+    c[1], c[2] = c[2], c[1]
+    cases.append((A.rowptr, c, A.val))  # unsorted row
+    v = A.val.copy()
+    v[1] *= 2
+    cases.append((A.rowptr, A.col, v))  # asymmetric value
+    v = A.val.copy()
+    v[0] = np.nan
+    cases.append((A.rowptr, A.col, v))  # not finite
+    v = A.val.copy()
+    v[0] = -4.0
+    cases.append((A.rowptr, A.col, v))  # non-positive diagonal
+    c = A.col.copy()
+    c[-1] = A.n + 5
+    cases.append((A.rowptr, c, A.val))  # column out of range
+    rp = A.rowptr.copy()
+    rp[3], rp[4] = rp[4], rp[3]
+    cases.append((rp, A.col, A.val))  # decreasing row pointer
+    for rp, c, v in cases:
+        with pytest.raises(U.UaamgError) as e:
+            U.uaamg_setup(rp, c, v)
+        assert e.value.status == 2
+
+
+def test_device_pointers_and_streams(oracle):
+    import torch
+
+    A = I.grid3d(24, sigma=0.25, seed=2)
+    dev = torch.device("cuda:0")
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    cc = torch.from_numpy(A.col).to(dev)
+    vv = torch.from_numpy(A.val).to(dev)
+    s = torch.cuda.Stream()
+    p = U.uaamg_default_params(max_agg_size=0)
+    h = U.uaamg_setup(rp, cc, vv, p, stream=s)
+    H = oracle.Hierarchy(A.rowptr, A.col, A.val,
+                         oracle.Params(**{k: getattr(p, k) for k in OR_KEYS}))
+    try:
+        compare_hierarchy(h, H, oracle, p.seed)
+        b = torch.from_numpy(I.rhs_uniform(A.n, 1)).to(dev)
+        x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+        st, it, rr = U.uaamg_solve(h, b, x, 1e-8)
+        torch.cuda.synchronize()
+        Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+        xb = x.cpu().numpy()
+        bb = b.cpu().numpy()
+        assert st == 0 and np.linalg.norm(bb - Asp @ xb) <= 1e-8 * np.linalg.norm(bb) * 1.0001
+    finally:
+        U.uaamg_free(h)
+
+
+@pytest.mark.parametrize("which", ["laplace3d_128"])
+def test_full_size_parity(oracle, which):
+    """The benchmark workload at full size, device-resident inputs as the benchmark passes
+    them: the whole hierarchy bit-exact, and the mixed-precision solve to 1e-8."""
+    import torch
+
+    A = I.laplace3d_128()
+    dev = torch.device("cuda:0")
+    rp, cc, vv = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+    p = U.uaamg_default_params(max_agg_size=0)
+    h = U.uaamg_setup(rp, cc, vv, p)
+    H = oracle.Hierarchy(A.rowptr, A.col, A.val,
+                         oracle.Params(**{k: getattr(p, k) for k in OR_KEYS}))
+    try:
+        compare_hierarchy(h, H, oracle, p.seed)
+        b = torch.from_numpy(I.rhs_uniform(A.n, 2001)).to(dev)
+        x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+        st, it, rr = U.uaamg_solve(h, b, x, 1e-8)
+        Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+        xb, bb = x.cpu().numpy(), b.cpu().numpy()
+        assert st == 0 and np.linalg.norm(bb - Asp @ xb) <= 1e-8 * np.linalg.norm(bb) * 1.0001
+        assert it <= 30
+    finally:
+        U.uaamg_free(h)
