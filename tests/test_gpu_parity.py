@@ -117,7 +117,7 @@ def test_long_rows_cross_chunks(oracle):
 def test_two_level_operator_fp64(oracle):
     A = I.grid2d(40, 37)
     for pre, post in ((1, 1), (2, 2), (0, 1), (1, 0), (3, 2)):
-        h, H, _ = both(A, oracle, precision=U.UAAMG_FP64, max_levels=2, coarse_size=2000,
+        h, H, _ = both(A, oracle, precision=U.UAAMG_FP64, max_levels=2, coarse_size=64,
                        pre=pre, post=post)
         try:
             r = np.random.default_rng(pre * 7 + post).standard_normal(A.n)
