@@ -170,6 +170,28 @@ uint64_t uaamg_memory_in_use(void);
 
 const char* uaamg_status_string(int status);
 
+/* ---- aggregation without device allocation ------------------------------------------ */
+/*
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory (an external memory manager owns the device's memory, or the
+ * calling thread must not issue cudaMalloc/cudaFree while other work is in flight).
+ *
+ * Aggregates one graph level exactly as level 0 of uaamg_setup does (priorities, aggregation
+ * passes with size limit max_agg_size and pass_mode, ascending coarse numbering) and writes
+ * agg[i] = the coarse vertex of fine vertex i (device int32[n], caller-owned) and *nc (host)
+ * = the number of aggregates.  A is validated like in uaamg_setup and must be on the device
+ * (A->on_device = 1).  Nothing is allocated: all scratch lives in one static device array
+ * of about 12 MB that every GPU loading this library holds until the process exits, so
+ * A->n may be at most 262,144 (larger graphs return UAAMG_ERR_UNSUPPORTED before any device
+ * work).  The first call on a device looks up that array's address (cudaGetSymbolAddress)
+ * and should therefore come before any stream capture.  Every call shares the array and
+ * clears what must start at zero: calls whose work overlaps on the GPU (different streams,
+ * or different host threads) race and must be serialised by the caller.  The call
+ * synchronises `stream` twice (after validation and to read *nc).
+ */
+int uaamg_aggregate_static(const uaamg_csr* A, int32_t max_agg_size, int32_t pass_mode,
+                           uint64_t seed, int32_t* agg, int32_t* nc, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ EXPORTS = [
     "uaamg_get_pass_of", "uaamg_get_minv", "uaamg_apply_B", "uaamg_apply_K",
     "uaamg_residual_history", "uaamg_get_stats", "uaamg_set_profiling", "uaamg_get_profile",
     "uaamg_total_launches", "uaamg_set_memory_budget", "uaamg_memory_in_use",
-    "uaamg_status_string",
+    "uaamg_status_string", "uaamg_aggregate_static",
 ]
 
 
@@ -90,6 +90,8 @@ def lib() -> C.CDLL:
             "uaamg_set_memory_budget": (C.c_int, [U64]),
             "uaamg_memory_in_use": (U64, []),
             "uaamg_status_string": (C.c_char_p, [C.c_int]),
+            "uaamg_aggregate_static": (C.c_int, [C.POINTER(uaamg_csr), I32, I32, U64, P,
+                                                 C.POINTER(I32), P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -262,3 +264,19 @@ def uaamg_set_memory_budget(nbytes: int):
 
 def uaamg_memory_in_use() -> int:
     return int(lib().uaamg_memory_in_use())
+
+
+def uaamg_aggregate_static(rowptr, col, val, agg, max_agg_size: int = 5,
+                           pass_mode: int = UAAMG_PASS_SINGLE_ROUND, seed: int = 0x5EED,
+                           stream=None) -> int:
+    """Level-0 aggregation into the caller's device buffer `agg` (int32[n]) with no device
+    allocation by the library; returns the number of aggregates.  All arrays are CUDA
+    tensors."""
+    (rp, d0), (cp, d1), (vp, d2), (ap, d3) = _ptr(rowptr), _ptr(col), _ptr(val), _ptr(agg)
+    if not (d0 and d1 and d2 and d3):
+        raise ValueError("uaamg_aggregate_static takes device arrays only")
+    A = uaamg_csr(int(rowptr.shape[0]) - 1, int(col.shape[0]), rp, cp, vp, 1)
+    nc = C.c_int32(0)
+    check(lib().uaamg_aggregate_static(C.byref(A), max_agg_size, pass_mode, seed, ap,
+                                       C.byref(nc), _stream(stream)), "uaamg_aggregate_static")
+    return nc.value
