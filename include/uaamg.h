@@ -80,6 +80,15 @@ typedef struct uaamg_params {
     int32_t max_iter;     /* outer iterations; default 200 */
     int32_t use_graphs;   /* 1 (default): replay each outer iteration as a CUDA graph */
     int32_t profile_class; /* UAAMG_KCLASS_* to time from setup on (0 = none, default) */
+    int32_t agg_repeat;   /* 1 (default): one aggregation per level; 2: aggregate the coarse
+                             graph once more before forming the level (Section 3.3) */
+    double kcycle_ratio;  /* > 0: coarse level m takes its second flexible-CG step only when
+                             n_{m-1} / n_m >= kcycle_ratio; default 0 (always two steps) */
+    double min_coarsening; /* > 0: a level of at most 1024 unknowns whose aggregation would
+                              shrink it by less than this factor becomes the coarsest; 0 */
+    int32_t fuse_below;   /* coarse levels with at most this many unknowns run their K-cycle
+                             in one fused single-block kernel (pre = post = 1 only); 0 = off;
+                             default 8192 */
 } uaamg_params;
 
 typedef struct uaamg_handle uaamg_handle;

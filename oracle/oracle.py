@@ -38,7 +38,8 @@ class _Params(C.Structure):
     _fields_ = [("coarse_size", C.c_int32), ("max_levels", C.c_int32),
                 ("max_agg_size", C.c_int32), ("pass_mode", C.c_int32), ("seed", C.c_uint64),
                 ("pre", C.c_int32), ("post", C.c_int32), ("kcycle_inner", C.c_int32),
-                ("kcycle_tau", C.c_double), ("max_iter", C.c_int32)]
+                ("kcycle_tau", C.c_double), ("max_iter", C.c_int32), ("agg_repeat", C.c_int32),
+                ("kcycle_ratio", C.c_double), ("min_coarsening", C.c_double)]
 
 
 _lib = None
@@ -176,11 +177,14 @@ class Params:
     kcycle_inner: int = 2
     kcycle_tau: float = 0.0
     max_iter: int = 200
+    agg_repeat: int = 1
+    kcycle_ratio: float = 0.0
+    min_coarsening: float = 0.0
 
     def c(self) -> _Params:
         return _Params(self.coarse_size, self.max_levels, self.max_agg_size, self.pass_mode,
                        self.seed, self.pre, self.post, self.kcycle_inner, self.kcycle_tau,
-                       self.max_iter)
+                       self.max_iter, self.agg_repeat, self.kcycle_ratio, self.min_coarsening)
 
 
 class Hierarchy:

@@ -29,8 +29,14 @@
  *    vertex k.
  *  - Levels are numbered 0 = finest.  Coarsening continues while n_l > coarse_size and the
  *    level count is below max_levels (Algorithm 1 setup loop).
+ *  - Aggregating twice per level (Section 3.3, equivalent to skipping a level): the second
+ *    stage aggregates the first stage's coarse matrix with priority salt index 2l+1 (the
+ *    first stage uses 2l), and is skipped when that matrix is already <= coarse_size.
  *  - K-cycle (Section 4.3): two flexible-CG steps on each coarse level, preconditioned by
  *    the next level's cycle, with the coarsest level solved exactly by dense Cholesky.
+ *    Optional safeguards the paper does not state (both off by default): one step only on
+ *    levels reached by weak coarsening (kcycle_ratio), and stopping the hierarchy when a
+ *    small level stops coarsening (min_coarsening).
  *  - Outer iteration (Section 1, Section 4.4): flexible CG with one stored direction,
  *    preconditioned by the K-cycle, stopped on the relative l2 residual of b - A x.
  */
@@ -328,6 +334,10 @@ typedef struct or_params {
     int32_t kcycle_inner; /* 1 or 2 flexible-CG steps per coarse level */
     double kcycle_tau;    /* > 0: skip the second step when |rho~| <= tau |rho| */
     int32_t max_iter;     /* outer iterations */
+    int32_t agg_repeat;   /* 1: one aggregation per level; 2: aggregate twice (Section 3.3) */
+    double kcycle_ratio;  /* > 0: level m takes its second step only if n_{m-1}/n_m >= this */
+    double min_coarsening; /* > 0: a level with n <= 1024 that would shrink by less than this
+                              factor becomes the coarsest */
 } or_params;
 
 typedef struct or_level {
@@ -354,7 +364,8 @@ void* or_setup(int32_t n, const int32_t* rowptr, const int32_t* col, const doubl
     *status = OR_ERR_ARG;
     if (n < 1 || p->coarse_size < 1 || p->max_levels < 1 || p->max_levels > OR_MAX_LEVELS ||
         p->max_agg_size < 0 || p->max_agg_size == 1 || p->pre < 0 || p->post < 0 ||
-        p->kcycle_inner < 1 || p->kcycle_inner > 2 || p->max_iter < 0)
+        p->kcycle_inner < 1 || p->kcycle_inner > 2 || p->max_iter < 0 ||
+        p->agg_repeat < 1 || p->agg_repeat > 2 || p->kcycle_ratio < 0 || p->min_coarsening < 0)
         return NULL;
     or_hier* h = (or_hier*)calloc(1, sizeof(or_hier));
     h->p = *p;
@@ -371,11 +382,13 @@ void* or_setup(int32_t n, const int32_t* rowptr, const int32_t* col, const doubl
     int32_t l = 0;
     while (h->lev[l].n > p->coarse_size && l + 1 < p->max_levels) {
         or_level* F = &h->lev[l];
+        /* stage 1: aggregate the level's graph (priority salt index l, or 2l when twice) */
+        const int32_t stage_salt = (p->agg_repeat == 2) ? 2 * l : l;
         uint64_t* P = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)F->n);
         int32_t* root_of = (int32_t*)malloc(sizeof(int32_t) * (size_t)F->n);
         F->pass_of = (int32_t*)malloc(sizeof(int32_t) * (size_t)F->n);
         F->agg = (int32_t*)malloc(sizeof(int32_t) * (size_t)F->n);
-        or_priorities(F->n, F->rowptr, F->col, p->seed, l, P);
+        or_priorities(F->n, F->rowptr, F->col, p->seed, stage_salt, P);
         F->passes = or_paa(F->n, F->rowptr, F->col, P, p->max_agg_size, p->pass_mode, root_of,
                            F->pass_of);
         F->nc = or_renumber(F->n, root_of, F->agg);
@@ -394,6 +407,55 @@ void* or_setup(int32_t n, const int32_t* rowptr, const int32_t* col, const doubl
         C->val = (double*)malloc(sizeof(double) * (size_t)(F->nnz > 0 ? F->nnz : 1));
         C->nnz = or_coarse(F->n, F->rowptr, F->col, F->val, F->agg, F->nc, C->rowptr, C->col,
                            C->val, F->nnz);
+        /* stage 2 (Section 3.3, aggregation applied twice = one level skipped): aggregate the
+         * intermediate matrix C again; the level's aggregates are the unions, agg = agg2[agg1],
+         * and the next matrix is Eq. (2.4) applied to C with agg2. */
+        if (p->agg_repeat == 2 && C->n > p->coarse_size) {
+            uint64_t* P2 = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)C->n);
+            int32_t* root2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)C->n);
+            int32_t* pass2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)C->n);
+            int32_t* agg2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)C->n);
+            or_priorities(C->n, C->rowptr, C->col, p->seed, 2 * l + 1, P2);
+            or_paa(C->n, C->rowptr, C->col, P2, p->max_agg_size, p->pass_mode, root2, pass2);
+            int32_t nc2 = or_renumber(C->n, root2, agg2);
+            if (nc2 < C->n) {
+                int32_t* rp2 = (int32_t*)malloc(sizeof(int32_t) * ((size_t)nc2 + 1));
+                int32_t* col2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(C->nnz > 0 ? C->nnz : 1));
+                double* val2 = (double*)malloc(sizeof(double) * (size_t)(C->nnz > 0 ? C->nnz : 1));
+                int64_t z2 = or_coarse(C->n, C->rowptr, C->col, C->val, agg2, nc2, rp2, col2,
+                                       val2, C->nnz);
+                for (int32_t i = 0; i < F->n; i++) F->agg[i] = agg2[F->agg[i]];
+                F->nc = nc2;
+                free(C->rowptr);
+                free(C->col);
+                free(C->val);
+                C->n = nc2;
+                C->nnz = z2;
+                C->rowptr = rp2;
+                C->col = col2;
+                C->val = val2;
+            }
+            free(P2);
+            free(root2);
+            free(pass2);
+            free(agg2);
+        }
+        /* stagnating coarsening: keep this level as the coarsest when it is small enough */
+        if (p->min_coarsening > 0.0 && F->n <= 1024 &&
+            (double)F->n < p->min_coarsening * (double)F->nc) {
+            free(C->rowptr);
+            free(C->col);
+            free(C->val);
+            C->rowptr = NULL;
+            C->col = NULL;
+            C->val = NULL;
+            C->n = 0;
+            C->nnz = 0;
+            free(F->agg);
+            F->agg = NULL;
+            F->nc = 0;
+            break;
+        }
         l++;
     }
     h->nlev = l + 1;
@@ -540,6 +602,9 @@ static void apply_K(const or_hier* h, int32_t m, const double* rho, double* e) {
     double a1 = alpha1 / rho1;
     for (int32_t i = 0; i < n; i++) rt[i] = rho[i] - a1 * v1[i];
     int second = (h->p.kcycle_inner == 2);
+    if (second && h->p.kcycle_ratio > 0.0 &&
+        (double)h->lev[m - 1].n < h->p.kcycle_ratio * (double)L->n)
+        second = 0; /* weak coarsening into level m: one step */
     if (second && h->p.kcycle_tau > 0.0) {
         double nr = sqrt(dot(n, rt, rt)), n0 = sqrt(dot(n, rho, rho));
         if (nr <= h->p.kcycle_tau * n0) second = 0;

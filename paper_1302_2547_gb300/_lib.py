@@ -39,7 +39,9 @@ class uaamg_params(C.Structure):
                 ("max_agg_size", C.c_int32), ("pass_mode", C.c_int32), ("seed", C.c_uint64),
                 ("pre", C.c_int32), ("post", C.c_int32), ("kcycle_inner", C.c_int32),
                 ("kcycle_tau", C.c_double), ("precision", C.c_int32), ("max_iter", C.c_int32),
-                ("use_graphs", C.c_int32), ("profile_class", C.c_int32)]
+                ("use_graphs", C.c_int32), ("profile_class", C.c_int32),
+                ("agg_repeat", C.c_int32), ("kcycle_ratio", C.c_double),
+                ("min_coarsening", C.c_double), ("fuse_below", C.c_int32)]
 
 
 class uaamg_stats(C.Structure):

@@ -69,7 +69,9 @@ static bool params_ok(const uaamg_params* p) {
            p->pre >= 0 && p->pre <= 8 && p->post >= 0 && p->post <= 8 &&
            (p->kcycle_inner == 1 || p->kcycle_inner == 2) && p->kcycle_tau >= 0.0 &&
            (p->precision == UAAMG_FP64 || p->precision == UAAMG_MIXED) && p->max_iter >= 0 &&
-           p->profile_class >= 0 && p->profile_class <= UAAMG_KCLASS_COARSE;
+           p->profile_class >= 0 && p->profile_class <= UAAMG_KCLASS_COARSE &&
+           (p->agg_repeat == 1 || p->agg_repeat == 2) && p->kcycle_ratio >= 0.0 &&
+           p->min_coarsening >= 0.0 && p->fuse_below >= 0;
 }
 
 }  // namespace uaamg
@@ -94,6 +96,10 @@ void uaamg_default_params(uaamg_params* p) {
     p->max_iter = 200;
     p->use_graphs = 1;
     p->profile_class = 0;
+    p->agg_repeat = 1;
+    p->kcycle_ratio = 0.0;
+    p->min_coarsening = 0.0;
+    p->fuse_below = kTailMaxN;
 }
 
 int uaamg_setup(const uaamg_csr* A, const uaamg_params* p, void* stream, uaamg_handle** out) {

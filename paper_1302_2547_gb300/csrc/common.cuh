@@ -84,6 +84,16 @@ struct Level {
     LevelScalars* sc = nullptr;
 };
 
+// Device descriptor of one level for the fused small-level K-cycle (kern_tail.cu).
+struct TailLevel {
+    int n, inner;
+    const int *rowptr, *col, *agg, *aggptr, *members;
+    const void *val, *minv;
+    void *rhs, *out, *w, *s, *c1, *v1, *rt, *c2, *v2;
+};
+
+constexpr int kTailMaxN = 8192;  // default size below which levels run fused in one block
+
 struct ProfSlot {
     cudaEvent_t a, b;
 };
@@ -106,6 +116,9 @@ struct Handle {
     Ctrl* ctrl = nullptr;
     double* partials = nullptr;
     size_t partials_cap = 0;
+    // fused small-level K-cycle: first level handled by k_tail (0 = none)
+    int tail_level = 0;
+    TailLevel* tail_dev = nullptr;
     // graph of one outer iteration
     cudaGraphExec_t graph = nullptr;
     long long graph_nodes = 0;

@@ -479,6 +479,70 @@ int launch_coarse_compact(Handle* h, int nc, const int* off, const int* rowptr_c
 }
 
 // ---------------------------------------------------------------------------------------
+// Aggregating twice (Section 3.3): the level's aggregates are unions of first-stage
+// aggregates, agg = agg2[agg1]; the member list of each union is kept in ascending fine
+// index, as for a single stage.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+k_compose_sizes(int nc, const int* __restrict__ aggptr2, const int* __restrict__ members2,
+                const int* __restrict__ aggptr1, int* __restrict__ sizes) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int s = 0;
+    for (int q = aggptr2[I]; q < aggptr2[I + 1]; q++) {
+        int J = members2[q];
+        s += aggptr1[J + 1] - aggptr1[J];
+    }
+    sizes[I] = s;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_compose_members(int nc, const int* __restrict__ aggptr2, const int* __restrict__ members2,
+                  const int* __restrict__ aggptr1, const int* __restrict__ members1,
+                  const int* __restrict__ aggptr, int* tmp, int* __restrict__ members) {
+    const int lane = threadIdx.x & 31;
+    const int I = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (I >= nc) return;
+    const int base = aggptr[I];
+    int m = 0;
+    for (int q = aggptr2[I]; q < aggptr2[I + 1]; q++) {
+        const int J = members2[q];
+        const int k0 = aggptr1[J], k1 = aggptr1[J + 1];
+        for (int k = k0 + lane; k < k1; k += 32) tmp[base + m + (k - k0)] = members1[k];
+        m += k1 - k0;
+    }
+    __syncwarp();
+    for (int e = lane; e < m; e += 32) {  // distinct values: rank = number of smaller ones
+        const int v = __ldcg(tmp + base + e);
+        int rank = 0;
+        for (int f = 0; f < m; f++) rank += (__ldcg(tmp + base + f) < v);
+        members[base + rank] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_compose_agg(int n, const int* __restrict__ agg1, const int* __restrict__ agg2,
+              int* __restrict__ agg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) agg[i] = agg2[agg1[i]];
+}
+
+int launch_compose(Handle* h, int n, int nc, const int* agg1, const int* aggptr1,
+                   const int* members1, const int* agg2, const int* aggptr2,
+                   const int* members2, int* agg, int* aggptr, int* members, int* tmp,
+                   int* scan_tmp) {
+    k_compose_sizes<<<grid_for(nc, kThreads), kThreads, 0, h->work>>>(nc, aggptr2, members2, aggptr1, aggptr);
+    count_launch(h);
+    int st = scan_exclusive(h, aggptr, aggptr, nc, aggptr + nc, scan_tmp);
+    if (st) return st;
+    k_compose_members<<<grid_for((long long)nc * 32, kThreads), kThreads, 0, h->work>>>(
+        nc, aggptr2, members2, aggptr1, members1, aggptr, tmp, members);
+    k_compose_agg<<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, agg1, agg2, agg);
+    count_launch(h, 2);
+    return check_cuda(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------------------
 // l1-Jacobi data, Section 4.1: Minv_i = 1 / (a_ii + sum_{j!=i} |a_ij|), the row sum taken in
 // stored order; FP32 copies for the mixed-precision cycle.
 // ---------------------------------------------------------------------------------------

@@ -24,6 +24,23 @@ __device__ __forceinline__ T rb_gather(const RBArgs<T>& a, int j) {
     else return a.x[j];
 }
 
+// Four consecutive matrix values with one 16-byte (FP32) or two 16-byte (FP64) loads.
+__device__ __forceinline__ void ld_val4(const float* p, float (&v)[4]) {
+    const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+}
+__device__ __forceinline__ void ld_val4(const double* p, double (&v)[4]) {
+    const double2 q0 = __ldcs(reinterpret_cast<const double2*>(p));
+    const double2 q1 = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = q0.x;
+    v[1] = q0.y;
+    v[2] = q1.x;
+    v[3] = q1.y;
+}
+
 template <typename T, int MODE, int ND>
 __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
     if (a.skip && *(volatile const int*)a.skip) return;
@@ -32,6 +49,7 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
     const int r1 = min(a.n, r0 + kRowsPerBlock);
     const int row = r0 + threadIdx.x;
     const int k0 = a.rowptr[r0], k1 = a.rowptr[r1];
+    const int ktot = a.rowptr[a.n];
     int rs = 0, re = 0;
     if (row < r1) {
         rs = a.rowptr[row];
@@ -40,10 +58,31 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
     T acc = T(0);
     for (int c0 = k0; c0 < k1; c0 += kChunk) {
         const int c1 = min(k1, c0 + kChunk);
-#pragma unroll 4
-        for (int k = c0 + threadIdx.x; k < c1; k += kThreads) {
-            const int j = ld_stream(a.col + k);
-            prod[k - c0] = mul_rn(ld_stream(a.val + k), rb_gather<T, MODE>(a, j));
+        // groups of four entries at 16-byte aligned indices; entries outside [c0, c1) are
+        // loaded (they lie inside the arrays) but not used
+#pragma unroll 2
+        for (int kb = (c0 & ~3) + 4 * (int)threadIdx.x; kb < c1; kb += 4 * kThreads) {
+            int j[4];
+            T v[4];
+            if (kb + 4 <= ktot) {
+                const int4 cj = __ldcs(reinterpret_cast<const int4*>(a.col + kb));
+                j[0] = cj.x;
+                j[1] = cj.y;
+                j[2] = cj.z;
+                j[3] = cj.w;
+                ld_val4(a.val + kb, v);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    j[e] = (kb + e < ktot) ? a.col[kb + e] : 0;
+                    v[e] = (kb + e < ktot) ? a.val[kb + e] : T(0);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int k = kb + e;
+                if (k >= c0 && k < c1) prod[k - c0] = mul_rn(v[e], rb_gather<T, MODE>(a, j[e]));
+            }
         }
         __syncthreads();
         const int lo = max(rs, c0), hi = min(re, c1);

@@ -1,0 +1,224 @@
+// kern_tail.cu -- the K-cycle of the small coarse levels in one kernel launch.
+//
+// Level m of the K-cycle (Section 4.3) is visited 2^(m-1) times per outer iteration (fewer
+// with one-step levels), and on small levels every step is a sub-microsecond kernel, so the
+// cycle becomes launch-bound.  From the first level with at most kTailMaxN unknowns down
+// to the coarsest, this kernel runs the whole recursion K_m -> B_m -> K_{m+1} ... in one
+// thread block of 1024 threads: each step of the launched path (fused SpMV + l1-Jacobi
+// sweeps, residual restriction, prolongation, the two flexible-CG steps and the exact
+// coarsest solve) becomes a block-wide phase separated by __syncthreads, with the same
+// arithmetic per entry and block-level fixed-order reductions for the inner products.
+// Vectors stay in the levels' global buffers (L2-resident at these sizes).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace uaamg {
+
+constexpr int kTailThreads = 1024;
+
+// Block-wide fixed-order sum of ND values; every thread receives the totals.
+template <int ND>
+__device__ __forceinline__ void block_sum(double (&v)[ND]) {
+    __shared__ double sh[ND][kTailThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+        double s = 0.0;
+        for (int w = 0; w < kTailThreads / 32; w++) s += sh[k][w];
+        v[k] = s;
+    }
+    __syncthreads();
+}
+
+// The recursion K_m -> B_m -> K_{m+1} runs as an explicit stack of frames in shared memory
+// (at most two frames per level), so the kernel needs no call stack.  Every thread reads
+// the top frame, the block executes one phase of it, and thread 0 pushes or pops.
+struct TailFrame {
+    int kind;   // 0: K_m, 1: B_m
+    int level;
+    int phase;
+    const void* in;
+    void* out;
+    double rho1, w1, w2;
+};
+constexpr int kTailMaxFrames = 2 * kMaxLevels;
+
+template <typename T>
+__device__ __forceinline__ void spmv_rows(const TailLevel& L, const T* x, T* y, int nd,
+                                          const T* da, const T* db, double* d) {
+    const T* val = (const T*)L.val;
+    for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
+        T acc = T(0);
+        for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; k++)
+            acc = add_rn(acc, mul_rn(val[k], x[L.col[k]]));
+        y[i] = acc;
+        const double xi = (double)x[i];
+        d[0] += xi * (double)acc;
+        if (nd >= 2) d[1] += xi * (double)da[i];
+        if (nd >= 3) d[2] += xi * (double)db[i];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads, 1)
+k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, const int* skip) {
+    if (skip && *(volatile const int*)skip) return;
+    __shared__ TailFrame st[kTailMaxFrames];
+    __shared__ int sp;
+    if (threadIdx.x == 0) {
+        st[0] = TailFrame{0, m0, 0, lv[m0].rhs, lv[m0].out, 0.0, 0.0, 0.0};
+        sp = 1;
+    }
+    __syncthreads();
+    while (true) {
+        const int top = sp;
+        if (top == 0) break;
+        const TailFrame f = st[top - 1];
+        __syncthreads();
+        const TailLevel& L = lv[f.level];
+        const T* in = (const T*)f.in;
+        T* out = (T*)f.out;
+        int push = 0, pop = 0, next_phase = f.phase;
+        TailFrame child{};
+        double rho1 = f.rho1, w1 = f.w1, w2 = f.w2;
+        if (f.kind == 0) {  // ---- K_m: two flexible-CG steps preconditioned by B_m ----
+            T *c1 = (T*)L.c1, *v1 = (T*)L.v1, *rt = (T*)L.rt, *c2 = (T*)L.c2, *v2 = (T*)L.v2;
+            if (f.level == nlev - 1) {  // exact solve with the dense inverse
+                for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
+                    double sum = 0.0;
+                    for (int j = 0; j < L.n; j++) sum += inv[(size_t)i * L.n + j] * (double)in[j];
+                    out[i] = (T)sum;
+                }
+                pop = 1;
+            } else if (f.phase == 0) {  // c1 = B_m(rho)
+                child = TailFrame{1, f.level, 0, in, c1, 0.0, 0.0, 0.0};
+                push = 1;
+                next_phase = 1;
+            } else if (f.phase == 1) {  // v1 = A c1; rho1, alpha1; rho~
+                double d[3] = {0.0, 0.0, 0.0};
+                spmv_rows<T>(L, c1, v1, 2, in, nullptr, d);
+                block_sum<3>(d);
+                rho1 = d[0];
+                w1 = 0.0;
+                w2 = 0.0;
+                bool second = false;
+                if (rho1 > 0.0) {
+                    w1 = d[1] / rho1;
+                    second = (L.inner >= 2);
+                    if (second) {
+                        const T a1t = (T)w1;
+                        double nr[2] = {0.0, 0.0};
+                        for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
+                            const T v = sub_rn(in[i], mul_rn(a1t, v1[i]));
+                            rt[i] = v;
+                            nr[0] += (double)v * (double)v;
+                            nr[1] += (double)in[i] * (double)in[i];
+                        }
+                        block_sum<2>(nr);
+                        if (tau > 0.0 && sqrt(nr[0]) <= tau * sqrt(nr[1])) second = false;
+                    }
+                }
+                if (second) {  // c2 = B_m(rho~)
+                    child = TailFrame{1, f.level, 0, rt, c2, 0.0, 0.0, 0.0};
+                    push = 1;
+                    next_phase = 2;
+                } else {
+                    next_phase = 3;
+                }
+            } else if (f.phase == 2) {  // v2 = A c2; beta, gamma, alpha2
+                double d[3] = {0.0, 0.0, 0.0};
+                spmv_rows<T>(L, c2, v2, 3, v1, rt, d);
+                block_sum<3>(d);
+                const double beta = d[0], gamma = d[1], alpha2 = d[2];
+                const double rho2 = beta - gamma * gamma / rho1;
+                if (rho2 > 0.0) {
+                    w1 = w1 - gamma * alpha2 / (rho1 * rho2);
+                    w2 = alpha2 / rho2;
+                }
+                next_phase = 3;
+            } else {  // e = w1 c1 + w2 c2
+                const T w1t = (T)w1, w2t = (T)w2;
+                for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
+                    T v = mul_rn(w1t, c1[i]);
+                    if (w2 != 0.0) v = add_rn(v, mul_rn(w2t, c2[i]));
+                    out[i] = v;
+                }
+                pop = 1;
+            }
+        } else {  // ---- B_l: pre-sweep, restriction, K_{l+1}, prolongation + post-sweep ----
+            const TailLevel& C = lv[f.level + 1];
+            const T* val = (const T*)L.val;
+            const T* minv = (const T*)L.minv;
+            T* x = (T*)L.w;
+            T* s = (T*)L.s;
+            T* rc = (T*)C.rhs;
+            T* ec = (T*)C.out;
+            if (f.phase == 0) {
+                for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
+                    T acc = T(0);
+                    for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; k++) {
+                        const int j = L.col[k];
+                        acc = add_rn(acc, mul_rn(val[k], mul_rn(minv[j], in[j])));
+                    }
+                    x[i] = mul_rn(minv[i], in[i]);
+                    s[i] = sub_rn(in[i], acc);
+                }
+                __syncthreads();
+                for (int I = threadIdx.x; I < C.n; I += kTailThreads) {
+                    T sum = T(0);
+                    for (int q = L.aggptr[I]; q < L.aggptr[I + 1]; q++)
+                        sum = add_rn(sum, s[L.members[q]]);
+                    rc[I] = sum;
+                }
+                child = TailFrame{0, f.level + 1, 0, rc, ec, 0.0, 0.0, 0.0};
+                push = 1;
+                next_phase = 1;
+            } else {
+                for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
+                    T acc = T(0);
+                    for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; k++) {
+                        const int j = L.col[k];
+                        acc = add_rn(acc, mul_rn(val[k], add_rn(x[j], ec[L.agg[j]])));
+                    }
+                    const T xi = add_rn(x[i], ec[L.agg[i]]);
+                    out[i] = add_rn(xi, mul_rn(minv[i], sub_rn(in[i], acc)));
+                }
+                pop = 1;
+            }
+        }
+        __syncthreads();  // this phase's global writes are visible to the whole block
+        if (threadIdx.x == 0) {
+            if (pop) {
+                sp = top - 1;
+            } else {
+                st[top - 1].phase = next_phase;
+                st[top - 1].rho1 = rho1;
+                st[top - 1].w1 = w1;
+                st[top - 1].w2 = w2;
+                if (push) {
+                    st[top] = child;
+                    sp = top + 1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+int launch_tail(Handle* h, int m0) {
+    k_tail<T><<<1, kTailThreads, 0, h->work>>>(h->tail_dev, m0, h->nlev, h->coarse_inv,
+                                               h->p.kcycle_tau, &h->ctrl->skip);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+template int launch_tail<float>(Handle*, int);
+template int launch_tail<double>(Handle*, int);
+
+}  // namespace uaamg

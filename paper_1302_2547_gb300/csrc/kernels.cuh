@@ -36,6 +36,10 @@ int launch_coarse_build(Handle* h, int level, int nc, const int* aggptr, const i
 int launch_coarse_compact(Handle* h, int nc, const int* off, const int* rowptr_c,
                           const int* cnt, const int* tJ, const double* tV, int* col_c,
                           double* val_c);
+int launch_compose(Handle* h, int n, int nc, const int* agg1, const int* aggptr1,
+                   const int* members1, const int* agg2, const int* aggptr2,
+                   const int* members2, int* agg, int* aggptr, int* members, int* tmp,
+                   int* scan_tmp);
 int launch_level_finish(Handle* h, int n, long long nnz, const int* rowptr, const int* col,
                         const double* val64, double* minv64, float* minv32, float* val32);
 int launch_dense_coarsest(Handle* h, int n, const int* rowptr, const int* col,
@@ -90,6 +94,10 @@ int launch_copy(Handle* h, int n, const T* in, T* out, const int* skip);
 template <typename T>
 int launch_prolong(Handle* h, int n, const T* x, const int* agg, const T* e, T* y,
                    const int* skip);
+
+// fused K-cycle of the levels m0 .. L-1 (kern_tail.cu)
+template <typename T>
+int launch_tail(Handle* h, int m0);
 
 // outer flexible CG (FP64 with the preconditioner output in T)
 int launch_cast_d2f(Handle* h, int n, const double* in, float* out);

@@ -31,11 +31,87 @@ static int read_back(Handle* h, const int* d_tot, HostReadback* hb) {
     return UAAMG_OK;
 }
 
+struct Scratch {
+    PaaBuffers pb;
+    int *f, *g, *mo, *cnt, *scan_tmp, *d_tot, *tJ, *sJ;
+    double *tV, *sV;
+};
+
+struct Csr {
+    int n = 0;
+    long long nnz = 0;
+    int* rowptr = nullptr;
+    int* col = nullptr;
+    double* val = nullptr;
+};
+
+struct Agg {
+    int nc = 0, passes = 0;
+    int *agg = nullptr, *aggptr = nullptr, *members = nullptr;
+};
+
+// One aggregation stage on graph G: priorities with the given salt, the passes of
+// Algorithm 2, ascending coarse numbering.  Outputs are handle temporaries.
+static int aggregate_stage(Handle* h, int prof_level, const Csr& G, uint32_t salt, Scratch& S,
+                           uint64_t* prio, int* pass_of, HostReadback* hb, Agg* out) {
+    int st;
+    if ((st = launch_priority(h, G.n, G.rowptr, G.col, salt, prio))) return st;
+    if ((st = launch_paa(h, prof_level, G.n, G.rowptr, G.col, prio, h->p.max_agg_size,
+                         h->p.pass_mode, S.pb, pass_of)))
+        return st;
+    if ((st = launch_root_flags(h, G.n, S.pb.root_of, S.pb.agg_size, S.f, S.g))) return st;
+    if ((st = scan_exclusive(h, S.f, S.f, G.n, S.d_tot + 0, S.scan_tmp))) return st;
+    if ((st = scan_exclusive(h, S.g, S.g, G.n, nullptr, S.scan_tmp))) return st;
+    if ((st = read_back(h, S.d_tot, hb))) return st;
+    out->passes = hb->ctrl.npasses;
+    out->nc = hb->nc;
+    if (out->nc >= G.n) return UAAMG_OK;  // no coarsening possible
+    out->agg = dalloc<int>(h, G.n, &st, true);
+    out->aggptr = dalloc<int>(h, out->nc + 1, &st, true);
+    out->members = dalloc<int>(h, G.n, &st, true);
+    if (st) return st;
+    return launch_renumber(h, G.n, S.pb.root_of, S.f, S.g, G.rowptr, G.col, S.d_tot + 0,
+                           out->agg, out->aggptr, out->members);
+}
+
+// Coarse operator of G under the aggregation `a` (Eq. 2.4) into C (handle temporaries).
+static int assemble(Handle* h, int prof_level, const Csr& G, const Agg& a, Scratch& S,
+                    HostReadback* hb, Csr* C) {
+    int st;
+    const int nc = a.nc;
+    if ((st = launch_coarse_m(h, nc, a.aggptr, a.members, G.rowptr, S.mo))) return st;
+    if ((st = scan_exclusive(h, S.mo, S.mo, nc, S.d_tot + 1, S.scan_tmp))) return st;
+    if ((st = launch_coarse_build(h, prof_level, nc, a.aggptr, a.members, G.rowptr, G.col, G.val,
+                                  a.agg, S.mo, S.tJ, S.tV, S.sJ, S.sV, S.cnt)))
+        return st;
+    C->n = nc;
+    C->rowptr = dalloc<int>(h, nc + 1, &st, true);
+    if (st) return st;
+    if ((st = scan_exclusive(h, S.cnt, C->rowptr, nc, S.d_tot + 2, S.scan_tmp))) return st;
+    cudaMemcpyAsync(C->rowptr + nc, S.d_tot + 2, sizeof(int), cudaMemcpyDeviceToDevice, h->work);
+    if ((st = read_back(h, S.d_tot, hb))) return st;
+    C->nnz = hb->nnzc;
+    C->col = dalloc<int>(h, C->nnz, &st, true);
+    C->val = dalloc<double>(h, C->nnz, &st, true);
+    if (st) return st;
+    return launch_coarse_compact(h, nc, S.mo, C->rowptr, S.cnt, S.tJ, S.tV, C->col, C->val);
+}
+
+template <typename T>
+static T* keep(Handle* h, const T* src, size_t count, int* st) {
+    T* dst = dalloc<T>(h, count, st);
+    if (*st == UAAMG_OK)
+        *st = check_cuda(cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyDeviceToDevice,
+                                         h->work));
+    return dst;
+}
+
 int build_hierarchy(Handle* h, const uaamg_csr* A) {
     int st = UAAMG_OK;
     const int n0 = A->n;
     const long long z0 = A->nnz;
     const bool mixed = (h->p.precision == UAAMG_MIXED);
+    const bool twice = (h->p.agg_repeat == 2);
     HostReadback* hb = nullptr;
     if (cudaMallocHost(&hb, sizeof(HostReadback)) != cudaSuccess) return UAAMG_ERR_OOM;
     memset(hb, 0, sizeof(HostReadback));
@@ -59,74 +135,88 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
         if ((st = launch_validate(h, n0, (int)z0, L.rowptr, L.col, L.val64))) goto done;
     }
     {
-        // setup scratch, sized for level 0 (every coarser level is smaller)
-        PaaBuffers pb;
-        pb.state = dalloc<uint8_t>(h, n0, &st, true);
-        pb.b1 = dalloc<uint64_t>(h, n0, &st, true);
-        pb.blocked = dalloc<uint8_t>(h, n0, &st, true);
-        pb.root_of = dalloc<int>(h, n0, &st, true);
-        pb.agg_size = dalloc<int>(h, n0, &st, true);
-        pb.slots = dalloc<int>(h, kMaxRoundSlots, &st, true);
-        int* f = dalloc<int>(h, n0, &st, true);
-        int* g = dalloc<int>(h, n0, &st, true);
-        int* mo = dalloc<int>(h, n0, &st, true);
-        int* cnt = dalloc<int>(h, n0, &st, true);
-        int* scan_tmp = dalloc<int>(h, scan_scratch_ints(n0), &st, true);
-        int* d_tot = dalloc<int>(h, 4, &st, true);
-        int* tJ = dalloc<int>(h, z0, &st, true);
-        int* sJ = dalloc<int>(h, z0, &st, true);
-        double* tV = dalloc<double>(h, z0, &st, true);
-        double* sV = dalloc<double>(h, z0, &st, true);
+        // setup scratch, sized for level 0 (every coarser graph is smaller)
+        Scratch S;
+        S.pb.state = dalloc<uint8_t>(h, n0, &st, true);
+        S.pb.b1 = dalloc<uint64_t>(h, n0, &st, true);
+        S.pb.blocked = dalloc<uint8_t>(h, n0, &st, true);
+        S.pb.root_of = dalloc<int>(h, n0, &st, true);
+        S.pb.agg_size = dalloc<int>(h, n0, &st, true);
+        S.pb.slots = dalloc<int>(h, kMaxRoundSlots, &st, true);
+        S.f = dalloc<int>(h, n0, &st, true);
+        S.g = dalloc<int>(h, n0, &st, true);
+        S.mo = dalloc<int>(h, n0, &st, true);
+        S.cnt = dalloc<int>(h, n0, &st, true);
+        S.scan_tmp = dalloc<int>(h, scan_scratch_ints(n0), &st, true);
+        S.d_tot = dalloc<int>(h, 4, &st, true);
+        S.tJ = dalloc<int>(h, z0, &st, true);
+        S.sJ = dalloc<int>(h, z0, &st, true);
+        S.tV = dalloc<double>(h, z0, &st, true);
+        S.sV = dalloc<double>(h, z0, &st, true);
         if (st) goto done;
-        if ((st = read_back(h, d_tot, hb))) goto done;  // validation result
+        if ((st = read_back(h, S.d_tot, hb))) goto done;  // validation result
 
         int l = 0;
         while (h->lev[l].n > h->p.coarse_size && l + 1 < h->p.max_levels && l + 1 < kMaxLevels) {
             Level& F = h->lev[l];
+            Csr G{F.n, F.nnz, F.rowptr, F.col, F.val64};
             F.prio = dalloc<uint64_t>(h, F.n, &st);
             F.pass_of = dalloc<int>(h, F.n, &st);
             if (st) goto done;
-            // priorities (Eq. 3.2) and aggregation passes (Algorithm 2)
-            if ((st = launch_priority(h, F.n, F.rowptr, F.col, level_salt(h->p.seed, l), F.prio)))
+            // stage 1: priorities (Eq. 3.2) and aggregation passes (Algorithm 2) on the level
+            Agg a1;
+            if ((st = aggregate_stage(h, l, G, level_salt(h->p.seed, twice ? 2 * l : l), S, F.prio,
+                                      F.pass_of, hb, &a1)))
                 goto done;
-            if ((st = launch_paa(h, l, F.n, F.rowptr, F.col, F.prio, h->p.max_agg_size,
-                                 h->p.pass_mode, pb, F.pass_of)))
-                goto done;
-            // coarse numbering by ascending root (Section 5.1)
-            if ((st = launch_root_flags(h, F.n, pb.root_of, pb.agg_size, f, g))) goto done;
-            if ((st = scan_exclusive(h, f, f, F.n, d_tot + 0, scan_tmp))) goto done;
-            if ((st = scan_exclusive(h, g, g, F.n, nullptr, scan_tmp))) goto done;
-            if ((st = read_back(h, d_tot, hb))) goto done;
-            F.passes = hb->ctrl.npasses;
-            const int nc = hb->nc;
-            if (nc >= F.n) break;  // no coarsening possible: F is the coarsest level
-            F.nc = nc;
-            F.agg = dalloc<int>(h, F.n, &st);
-            F.aggptr = dalloc<int>(h, nc + 1, &st);
-            F.members = dalloc<int>(h, F.n, &st);
-            if (st) goto done;
-            if ((st = launch_renumber(h, F.n, pb.root_of, f, g, F.rowptr, F.col, d_tot + 0, F.agg,
-                                      F.aggptr, F.members)))
-                goto done;
-            // coarse operator by aggregate sums (Eq. 2.4)
-            if ((st = launch_coarse_m(h, nc, F.aggptr, F.members, F.rowptr, mo))) goto done;
-            if ((st = scan_exclusive(h, mo, mo, nc, d_tot + 1, scan_tmp))) goto done;
-            if ((st = launch_coarse_build(h, l, nc, F.aggptr, F.members, F.rowptr, F.col, F.val64,
-                                          F.agg, mo, tJ, tV, sJ, sV, cnt)))
-                goto done;
+            F.passes = a1.passes;
+            if (a1.nc >= F.n) break;  // no coarsening possible: F is the coarsest level
+            Csr C1;
+            if ((st = assemble(h, l, G, a1, S, hb, &C1))) goto done;
+            Agg fin = a1;
+            Csr Cfin = C1;
+            // stage 2 (Section 3.3): aggregate the intermediate graph once more
+            if (twice && C1.n > h->p.coarse_size) {
+                uint64_t* prio2 = dalloc<uint64_t>(h, C1.n, &st, true);
+                int* pass2 = dalloc<int>(h, C1.n, &st, true);
+                if (st) goto done;
+                Agg a2;
+                if ((st = aggregate_stage(h, -1, C1, level_salt(h->p.seed, 2 * l + 1), S, prio2,
+                                          pass2, hb, &a2)))
+                    goto done;
+                if (a2.nc < C1.n) {
+                    Csr C2;
+                    if ((st = assemble(h, -1, C1, a2, S, hb, &C2))) goto done;
+                    Agg comp;
+                    comp.nc = a2.nc;
+                    comp.agg = dalloc<int>(h, F.n, &st, true);
+                    comp.aggptr = dalloc<int>(h, a2.nc + 1, &st, true);
+                    comp.members = dalloc<int>(h, F.n, &st, true);
+                    int* ctmp = dalloc<int>(h, F.n, &st, true);
+                    if (st) goto done;
+                    if ((st = launch_compose(h, F.n, a2.nc, a1.agg, a1.aggptr, a1.members, a2.agg,
+                                             a2.aggptr, a2.members, comp.agg, comp.aggptr,
+                                             comp.members, ctmp, S.scan_tmp)))
+                        goto done;
+                    fin = comp;
+                    Cfin = C2;
+                }
+            }
+            // stagnating coarsening: a small level that barely shrinks becomes the coarsest
+            if (h->p.min_coarsening > 0.0 && F.n <= kMaxCoarsest &&
+                (double)F.n < h->p.min_coarsening * (double)fin.nc)
+                break;
+            // keep the level's aggregation and the next level's matrix
+            F.nc = fin.nc;
+            F.agg = keep<int>(h, fin.agg, F.n, &st);
+            F.aggptr = keep<int>(h, fin.aggptr, fin.nc + 1, &st);
+            F.members = keep<int>(h, fin.members, F.n, &st);
             Level& C = h->lev[l + 1];
-            C.n = nc;
-            C.rowptr = dalloc<int>(h, nc + 1, &st);
+            C.n = Cfin.n;
+            C.nnz = Cfin.nnz;
+            C.rowptr = keep<int>(h, Cfin.rowptr, Cfin.n + 1, &st);
+            C.col = keep<int>(h, Cfin.col, Cfin.nnz, &st);
+            C.val64 = keep<double>(h, Cfin.val, Cfin.nnz, &st);
             if (st) goto done;
-            if ((st = scan_exclusive(h, cnt, C.rowptr, nc, d_tot + 2, scan_tmp))) goto done;
-            cudaMemcpyAsync(C.rowptr + nc, d_tot + 2, sizeof(int), cudaMemcpyDeviceToDevice, h->work);
-            if ((st = read_back(h, d_tot, hb))) goto done;
-            C.nnz = hb->nnzc;
-            C.col = dalloc<int>(h, C.nnz, &st);
-            C.val64 = dalloc<double>(h, C.nnz, &st);
-            if (st) goto done;
-            if ((st = launch_coarse_compact(h, nc, mo, C.rowptr, cnt, tJ, tV, C.col, C.val64)))
-                goto done;
             l++;
         }
         h->nlev = l + 1;
@@ -199,6 +289,52 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
             if (st) goto done;
         }
         if (cudaMallocHost(&h->osc_host, sizeof(OuterScalars)) != cudaSuccess) st = UAAMG_ERR_OOM;
+    }
+    {  // levels small enough for the fused K-cycle kernel (one pre- and post-sweep only)
+        int m0 = 0;
+        if (h->p.pre == 1 && h->p.post == 1)
+            for (int l = 1; l < h->nlev - 1; l++)
+                if (h->lev[l].n <= h->p.fuse_below) {
+                    m0 = l;
+                    break;
+                }
+        if (m0 > 0 && st == UAAMG_OK) {
+            std::vector<TailLevel> tl(h->nlev);
+            for (int l = 0; l < h->nlev; l++) {
+                const Level& L = h->lev[l];
+                TailLevel& t = tl[l];
+                memset(&t, 0, sizeof(t));
+                t.n = L.n;
+                int inner = h->p.kcycle_inner;
+                if (l >= 1 && inner == 2 && h->p.kcycle_ratio > 0.0 &&
+                    (double)h->lev[l - 1].n < h->p.kcycle_ratio * (double)L.n)
+                    inner = 1;
+                t.inner = inner;
+                t.rowptr = L.rowptr;
+                t.col = L.col;
+                t.agg = L.agg;
+                t.aggptr = L.aggptr;
+                t.members = L.members;
+                t.val = mixed ? (const void*)L.val32 : (const void*)L.val64;
+                t.minv = mixed ? (const void*)L.minv32 : (const void*)L.minv64;
+                t.rhs = L.rhs;
+                t.out = L.out;
+                t.w = L.w;
+                t.s = L.s;
+                t.c1 = L.c1;
+                t.v1 = L.v1;
+                t.rt = L.rt;
+                t.c2 = L.c2;
+                t.v2 = L.v2;
+            }
+            h->tail_dev = dalloc<TailLevel>(h, h->nlev, &st);
+            if (st == UAAMG_OK) {
+                st = check_cuda(cudaMemcpyAsync(h->tail_dev, tl.data(), sizeof(TailLevel) * h->nlev,
+                                                cudaMemcpyHostToDevice, h->work));
+                if (st == UAAMG_OK) st = check_cuda(cudaStreamSynchronize(h->work));
+                h->tail_level = m0;
+            }
+        }
     }
 done:
     dfree_temps(h);

@@ -159,6 +159,9 @@ template <typename T>
 static int apply_K(Handle* h, int m, const T* in, T* out) {
     const int* skip = &h->ctrl->skip;
     if (m == h->nlev - 1) return launch_dense_apply<T>(h, h->nco, h->coarse_inv, in, out, skip);
+    if (h->tail_level > 0 && m == h->tail_level && in == (const T*)h->lev[m].rhs &&
+        out == (T*)h->lev[m].out)
+        return launch_tail<T>(h, m);  // the rest of the cycle in one launch
     Level& L = h->lev[m];
     T *c1 = (T*)L.c1, *v1 = (T*)L.v1, *rt = (T*)L.rt, *c2 = (T*)L.c2, *v2 = (T*)L.v2;
     int st;
@@ -171,7 +174,10 @@ static int apply_K(Handle* h, int m, const T* in, T* out) {
         a.result = &L.sc->rho1;  // (c1, A c1), (c1, rho)
         if ((st = launch_rowblock<T>(h, RB_SPMV, 2, a))) return st;
     }
-    const int inner = h->p.kcycle_inner;
+    int inner = h->p.kcycle_inner;
+    if (inner == 2 && h->p.kcycle_ratio > 0.0 &&
+        (double)h->lev[m - 1].n < h->p.kcycle_ratio * (double)L.n)
+        inner = 1;  // level reached by weak coarsening: one step
     if ((st = launch_kc_rt<T>(h, m, L.n, in, v1, rt, L.sc, inner, h->p.kcycle_tau, h->ctrl)))
         return st;
     if (inner >= 2) {

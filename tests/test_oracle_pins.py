@@ -480,3 +480,72 @@ def test_iterations_roughly_flat_in_n(oracle, inputs):
         assert st == 0
         its.append(it)
     assert max(its) <= 1.6 * min(its) and max(its) <= 30, its
+
+
+# ---------------------------------------------------------------------------------------
+# Aggregating twice per level (Section 3.3) and the K-cycle safeguards
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("integer", [True, False])
+def test_double_aggregation_is_two_stages(oracle, inputs, integer):
+    """The level's aggregates are unions of first-stage aggregates (agg = agg2[agg1]) and the
+    next matrix is Eq. 2.4 applied twice; with integer weights it equals the one-shot dense
+    product (P1 P2)^T A (P1 P2) exactly."""
+    A = inputs.random_graph(400, 900, seed=5, integer_weights=integer)
+    H = oracle.Hierarchy(A.rowptr, A.col, A.val,
+                         oracle.Params(agg_repeat=2, max_agg_size=4, coarse_size=8))
+    P1 = oracle.priorities(A.rowptr, A.col, 0x5EED, level=0)
+    r1, _, _ = oracle.paa(A.rowptr, A.col, P1, t=4, mode=1)
+    a1, n1 = oracle.renumber(r1)
+    rp1, cc1, vv1 = oracle.coarse(A.rowptr, A.col, A.val, a1, n1)
+    P2 = oracle.priorities(rp1, cc1, 0x5EED, level=1)
+    r2, _, _ = oracle.paa(rp1, cc1, P2, t=4, mode=1)
+    a2, n2 = oracle.renumber(r2)
+    assert n2 < n1 and H.n(1) == n2
+    assert np.array_equal(H.agg(0), a2[a1])
+    rp2, cc2, vv2 = oracle.coarse(rp1, cc1, vv1, a2, n2)
+    hrp, hcc, hvv = H.csr(1)
+    assert np.array_equal(hrp, rp2) and np.array_equal(hcc, cc2) and np.array_equal(hvv, vv2)
+    P = BF.prolongator(a2[a1], n2)
+    dense = P.T @ A.dense() @ P
+    got = np.zeros((n2, n2))
+    got[np.repeat(np.arange(n2), np.diff(hrp)), hcc] = hvv
+    if integer:
+        assert np.array_equal(got, dense)
+    else:
+        assert np.allclose(got, dense, rtol=1e-12, atol=1e-12)
+
+
+def test_one_step_levels_under_the_ratio_rule(oracle, inputs):
+    """With kcycle_ratio above every coarsening ratio, K_1 is one flexible-CG step:
+    e = ((c1, rho) / (c1, A c1)) c1 with c1 = B_1 rho (dense two-level B_1)."""
+    A = inputs.grid2d(14, dirichlet=True)
+    H = oracle.Hierarchy(A.rowptr, A.col, A.val,
+                         oracle.Params(max_levels=3, coarse_size=8, kcycle_ratio=1e9))
+    assert H.num_levels == 3
+    rp, cc, vv = H.csr(1)
+    n1 = H.n(1)
+    A1 = np.zeros((n1, n1))
+    A1[np.repeat(np.arange(n1), np.diff(rp)), cc] = vv
+    rp2, cc2, vv2 = H.csr(2)
+    A2 = np.zeros((H.n(2), H.n(2)))
+    A2[np.repeat(np.arange(H.n(2)), np.diff(rp2)), cc2] = vv2
+    B1 = BF.two_grid_B(A1, H.agg(1), H.n(2), np.linalg.inv(A2))
+    rho = np.random.default_rng(3).standard_normal(n1)
+    c1 = B1 @ rho
+    assert np.allclose(H.apply_K(1, rho), (c1 @ rho) / (c1 @ A1 @ c1) * c1, rtol=1e-10,
+                       atol=1e-13)
+
+
+def test_stagnation_stop(oracle, inputs):
+    A = inputs.grid2d(64, dirichlet=True)
+    full = oracle.Hierarchy(A.rowptr, A.col, A.val)
+    stop = oracle.Hierarchy(A.rowptr, A.col, A.val, oracle.Params(min_coarsening=1e9))
+    # the first level with at most 1024 unknowns becomes the coarsest
+    first_small = next(l for l in range(full.num_levels) if full.n(l) <= 1024)
+    assert stop.num_levels == first_small + 1
+    assert [stop.n(l) for l in range(stop.num_levels)] == \
+           [full.n(l) for l in range(first_small + 1)]
+    b = inputs.rhs_uniform(A.n, 1)
+    x, it, rr, st, _ = stop.solve(b, 1e-10)
+    assert st == 0 and np.linalg.norm(b - A.dense() @ x) <= 1e-10 * np.linalg.norm(b) * 1.0001
