@@ -31,8 +31,8 @@ TOL = 1e-8
 WORKLOAD = "laplace3d_128^3 7-point, Dirichlet, lognormal(0.25) edge weights"
 # Method parameters of this workload: aggregates of at most 4 vertices, aggregation applied
 # twice per level (Section 3.3), one flexible-CG step on levels reached by coarsening
-# weaker than 3x, and a small level that shrinks by less than 1.5x becomes the coarsest.
-BENCH_PARAMS = dict(max_agg_size=4, agg_repeat=2, kcycle_ratio=3.0, min_coarsening=1.5)
+# weaker than 5x, and a small level that shrinks by less than 1.5x becomes the coarsest.
+BENCH_PARAMS = dict(max_agg_size=4, agg_repeat=2, kcycle_ratio=5.0, min_coarsening=1.5)
 
 # DRAM traffic per launch of the roofline kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel source it was taken on.
@@ -127,9 +127,12 @@ def workload():
     return A, b
 
 
+EAGER = False  # --eager: launch every kernel directly instead of replaying graphs
+
+
 def bench_params(U, precision, profile_class=0):
     return U.uaamg_default_params(precision=precision, profile_class=profile_class,
-                                  **BENCH_PARAMS)
+                                  use_graphs=0 if EAGER else 1, **BENCH_PARAMS)
 
 
 def run_gpu(args, rank, world):
@@ -193,7 +196,8 @@ def run_gpu(args, rank, world):
 
     # headline: mixed precision, with the roofline kernel's own events live in the timed region
     prof_cls = {"smooth0": U.UAAMG_KCLASS_SMOOTH0, "spmv64": U.UAAMG_KCLASS_SPMV64,
-                "paa": U.UAAMG_KCLASS_PAA, "coarse": U.UAAMG_KCLASS_COARSE}[args.roofline_kernel]
+                "paa": U.UAAMG_KCLASS_PAA, "coarse": U.UAAMG_KCLASS_COARSE,
+                "none": 0}[args.roofline_kernel]
     sampler = ClockSampler(dev.index)
     total_ms, lat, rec, launches = timed(U.UAAMG_MIXED, args.steps, args.warmup, prof_cls, sampler)
     # the plain one-at-a-time FP64 GPU path, same workload
@@ -201,6 +205,50 @@ def run_gpu(args, rank, world):
         p_total, p_lat, p_rec = None, [], []
     else:
         p_total, p_lat, p_rec, _ = timed(U.UAAMG_FP64, max(2, args.steps // 2), 1)
+
+    # batched: one setup and 16 right-hand sides solved together per step (mixed precision)
+    batched = None
+    if not args.skip_batched:
+        R = 16
+        rng = np.random.default_rng(2001)
+        Bb = torch.from_numpy(np.ascontiguousarray(rng.uniform(-1.0, 1.0, (A.n, R)))).to(dev)
+        Xb = torch.zeros_like(Bb)
+        Kb = max(2, args.steps // 2)
+        brec = []
+
+        def batched_step():
+            h = U.uaamg_setup(rp, cc, vv, bench_params(U, U.UAAMG_MIXED), stream=stream)
+            try:
+                st, its, rrs = U.uaamg_solve_many(h, Bb, Xb, TOL)
+                if st != 0:
+                    raise RuntimeError(f"batched solve status {st}")
+                s = U.uaamg_get_stats(h)
+                return int(its.max()), float(rrs.max()), s
+            finally:
+                U.uaamg_free(h)
+
+        batched_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(Kb):
+            brec.append(batched_step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) / 1000.0
+        import scipy.sparse as sp0
+
+        Asp0 = sp0.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+        Xh, Bh = Xb.cpu().numpy(), Bb.cpu().numpy()
+        worst = max(float(np.linalg.norm(Bh[:, r] - Asp0 @ Xh[:, r]) / np.linalg.norm(Bh[:, r]))
+                    for r in range(R))
+        batched = {"value": round(R * Kb * world / job_time(tb, world, dev), 3), "unit": "solves/s",
+                   "rhs_per_setup": R, "steps": Kb,
+                   "setup_ms": round(float(np.median([r[2]["setup_ms"] for r in brec])), 3),
+                   "solve_ms": round(float(np.median([r[2]["solve_ms"] for r in brec])), 3),
+                   "iterations_max": int(max(r[0] for r in brec)),
+                   "relres_host_fp64_max": worst}
 
     # check the last solution on the host in FP64
     import scipy.sparse as sp
@@ -278,6 +326,7 @@ def run_gpu(args, rank, world):
             "setup_ms": round(float(np.median([r[2]['setup_ms'] for r in p_rec])), 3),
             "solve_ms": round(float(np.median([r[2]['solve_ms'] for r in p_rec])), 3),
             "iterations": int(np.median([r[0] for r in p_rec]))},
+        "batched_mixed": batched,
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
         "clocks": sampler.summary(),
     }
@@ -310,11 +359,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="uaamg", choices=["uaamg", "reference"])
     ap.add_argument("--roofline-kernel", default="smooth0",
-                    choices=["smooth0", "spmv64", "paa", "coarse"])
+                    choices=["smooth0", "spmv64", "paa", "coarse", "none"])
+    ap.add_argument("--eager", action="store_true",
+                    help="no CUDA graphs (for profilers that cannot follow graph replays)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-plain", action="store_true", help="do not time the FP64 path")
+    ap.add_argument("--skip-batched", action="store_true", help="do not time solve_many")
     args = ap.parse_args()
+    global EAGER
+    EAGER = args.eager
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
 

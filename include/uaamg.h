@@ -87,8 +87,8 @@ typedef struct uaamg_params {
     double min_coarsening; /* > 0: a level of at most 1024 unknowns whose aggregation would
                               shrink it by less than this factor becomes the coarsest; 0 */
     int32_t fuse_below;   /* coarse levels with at most this many unknowns run their K-cycle
-                             in one fused single-block kernel (pre = post = 1 only); 0 = off;
-                             default 8192 */
+                             in one fused single-block kernel (pre = post = 1 only); 0 = off
+                             (default: on GB300 one block is slower than launching) */
 } uaamg_params;
 
 typedef struct uaamg_handle uaamg_handle;
@@ -118,6 +118,21 @@ int uaamg_setup(const uaamg_csr* A, const uaamg_params* p, void* stream, uaamg_h
  */
 int uaamg_solve(uaamg_handle* h, const double* b, double* x, double tol, int32_t use_guess,
                 int32_t* iters, double* relres);
+
+/*
+ * Solves A X = B for nrhs right-hand sides at once (1 <= nrhs <= 32), each column by the
+ * same algorithm as uaamg_solve from x0 = 0, with its own K-cycle coefficients, its own
+ * outer iteration and its own stopping test; every level's matrix is read once per sweep
+ * for all columns.  B and X are float64 arrays of n * nrhs in row-major [n][nrhs] order (the
+ * nrhs values of row i are contiguous), host or device pointers.  iters[nrhs] and
+ * relres[nrhs] (host) receive each column's outer iteration count and final relative
+ * residual of b - A x.  Returns UAAMG_OK when every column converged, else
+ * UAAMG_ERR_NO_CONVERGENCE with all outputs filled; UAAMG_ERR_UNSUPPORTED for nrhs > 32 or a
+ * handle set up with pre != 1 or post != 1.  Workspace for nrhs columns is allocated on the
+ * first call with that many columns and kept by the handle.
+ */
+int uaamg_solve_many(uaamg_handle* h, int32_t nrhs, const double* B, double* X, double tol,
+                     int32_t* iters, double* relres);
 
 /* Releases every device allocation of the handle (stream-ordered on its stream). */
 void uaamg_free(uaamg_handle* h);
@@ -178,6 +193,38 @@ int uaamg_set_memory_budget(uint64_t bytes);
 uint64_t uaamg_memory_in_use(void);
 
 const char* uaamg_status_string(int status);
+
+/* ---- solve service ------------------------------------------------------------------- */
+/*
+ * A solve service on the current device (the serving extension of the method; the paper has
+ * no counterpart).  Requests (CSR matrix, right-hand side, tolerance; host arrays, copied at
+ * submit) are queued; `workers` host threads, each with its own CUDA stream, take them in
+ * arrival order.  Hierarchies stay cached on the device, keyed by matrix_key (or, when it
+ * is 0, a 64-bit FNV-1a hash of n and the three CSR arrays); least recently used idle ones
+ * are freed to admit new ones within budget_bytes (0 = no budget; the budget is applied
+ * library-wide with uaamg_set_memory_budget while the server lives).  A request whose
+ * estimated hierarchy cannot fit the budget is answered with UAAMG_ERR_BUDGET; one that
+ * fits after eviction waits until memory frees.  Continuous batching: when a worker takes a
+ * request it also takes every queued request for the same matrix and tolerance (up to
+ * max_batch <= 32) and solves them together with uaamg_solve_many.  Each answer is the same
+ * algorithm as uaamg_solve on that matrix.
+ */
+typedef struct uaamg_server uaamg_server;
+int uaamg_server_create(const uaamg_params* p, uint64_t budget_bytes, int32_t workers,
+                        int32_t max_batch, uaamg_server** out);
+/* A->on_device must be 0.  *ticket identifies the request for poll / wait. */
+int uaamg_server_submit(uaamg_server* s, const uaamg_csr* A, uint64_t matrix_key,
+                        const double* b, double tol, uint64_t* ticket);
+int uaamg_server_poll(uaamg_server* s, uint64_t ticket, int32_t* done);
+/* Blocks until the request is answered; x (host, n) receives the solution, latency_ms the
+ * time from submit to answer, batch the number of requests solved together with it.
+ * Returns the request's status; the ticket is released. */
+int uaamg_server_wait(uaamg_server* s, uint64_t ticket, double* x, int32_t* iters,
+                      double* relres, double* latency_ms, int32_t* batch);
+int uaamg_server_stats(uaamg_server* s, uint64_t* done, uint64_t* batches, uint64_t* cache_hits,
+                       uint64_t* setups, uint64_t* rejected, int32_t* cached);
+/* Finishes the queued requests, joins the workers and frees every cached hierarchy. */
+void uaamg_server_destroy(uaamg_server* s);
 
 /* ---- aggregation without device allocation ------------------------------------------ */
 /*

@@ -25,7 +25,9 @@ EXPORTS = [
     "uaamg_get_pass_of", "uaamg_get_minv", "uaamg_apply_B", "uaamg_apply_K",
     "uaamg_residual_history", "uaamg_get_stats", "uaamg_set_profiling", "uaamg_get_profile",
     "uaamg_total_launches", "uaamg_set_memory_budget", "uaamg_memory_in_use",
-    "uaamg_status_string", "uaamg_aggregate_static",
+    "uaamg_status_string", "uaamg_aggregate_static", "uaamg_solve_many",
+    "uaamg_server_create", "uaamg_server_submit", "uaamg_server_poll", "uaamg_server_wait",
+    "uaamg_server_stats", "uaamg_server_destroy",
 ]
 
 
@@ -94,6 +96,17 @@ def lib() -> C.CDLL:
             "uaamg_status_string": (C.c_char_p, [C.c_int]),
             "uaamg_aggregate_static": (C.c_int, [C.POINTER(uaamg_csr), I32, I32, U64, P,
                                                  C.POINTER(I32), P]),
+            "uaamg_solve_many": (C.c_int, [P, I32, P, P, D, P, P]),
+            "uaamg_server_create": (C.c_int, [C.POINTER(uaamg_params), U64, I32, I32,
+                                              C.POINTER(P)]),
+            "uaamg_server_submit": (C.c_int, [P, C.POINTER(uaamg_csr), U64, P, D,
+                                              C.POINTER(U64)]),
+            "uaamg_server_poll": (C.c_int, [P, U64, C.POINTER(I32)]),
+            "uaamg_server_wait": (C.c_int, [P, U64, P, C.POINTER(I32), C.POINTER(D),
+                                            C.POINTER(D), C.POINTER(I32)]),
+            "uaamg_server_stats": (C.c_int, [P, C.POINTER(U64), C.POINTER(U64), C.POINTER(U64),
+                                             C.POINTER(U64), C.POINTER(U64), C.POINTER(I32)]),
+            "uaamg_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -163,6 +176,19 @@ def uaamg_solve(h, b, x, tol: float = 1e-8, use_guess: bool = False):
     if st not in (UAAMG_OK, UAAMG_ERR_NO_CONVERGENCE):
         check(st, "uaamg_solve")
     return st, int(it.value), float(rr.value)
+
+
+def uaamg_solve_many(h, B, X, tol: float = 1e-8):
+    """B, X: [n][nrhs] float64 (numpy or torch, host or device).  Returns
+    (status, iters[nrhs], relres[nrhs])."""
+    nrhs = int(B.shape[1])
+    it = np.zeros(nrhs, np.int32)
+    rr = np.zeros(nrhs)
+    st = lib().uaamg_solve_many(h, nrhs, _ptr(B)[0], _ptr(X)[0], tol, it.ctypes.data,
+                                rr.ctypes.data)
+    if st not in (UAAMG_OK, UAAMG_ERR_NO_CONVERGENCE):
+        check(st, "uaamg_solve_many")
+    return st, it, rr
 
 
 def uaamg_free(h):
@@ -282,3 +308,60 @@ def uaamg_aggregate_static(rowptr, col, val, agg, max_agg_size: int = 5,
     check(lib().uaamg_aggregate_static(C.byref(A), max_agg_size, pass_mode, seed, ap,
                                        C.byref(nc), _stream(stream)), "uaamg_aggregate_static")
     return nc.value
+
+
+class Server:
+    """uaamg_server_*: queued solves with a device-resident hierarchy cache and batching of
+    requests for the same matrix.  Arrays are host numpy arrays (copied at submit)."""
+
+    def __init__(self, params: uaamg_params | None = None, budget_bytes: int = 0,
+                 workers: int = 2, max_batch: int = 16):
+        self._s = C.c_void_p()
+        check(lib().uaamg_server_create(C.byref(params) if params is not None else None,
+                                        budget_bytes, workers, max_batch, C.byref(self._s)),
+              "uaamg_server_create")
+        self._n = {}
+
+    def submit(self, rowptr, col, val, b, tol: float = 1e-8, key: int = 0) -> int:
+        rowptr = np.ascontiguousarray(rowptr, np.int32)
+        col = np.ascontiguousarray(col, np.int32)
+        val = np.ascontiguousarray(val, np.float64)
+        b = np.ascontiguousarray(b, np.float64)
+        A = uaamg_csr(len(rowptr) - 1, len(col), rowptr.ctypes.data, col.ctypes.data,
+                      val.ctypes.data, 0)
+        t = C.c_uint64(0)
+        check(lib().uaamg_server_submit(self._s, C.byref(A), key, b.ctypes.data, tol,
+                                        C.byref(t)), "uaamg_server_submit")
+        self._n[t.value] = len(rowptr) - 1
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = C.c_int32(0)
+        check(lib().uaamg_server_poll(self._s, ticket, C.byref(d)), "uaamg_server_poll")
+        return bool(d.value)
+
+    def wait(self, ticket: int):
+        """Returns (status, x, iters, relres, latency_ms, batch)."""
+        x = np.zeros(self._n.pop(ticket))
+        it, rr, lat, bt = C.c_int32(), C.c_double(), C.c_double(), C.c_int32()
+        st = lib().uaamg_server_wait(self._s, ticket, x.ctypes.data, C.byref(it), C.byref(rr),
+                                     C.byref(lat), C.byref(bt))
+        return st, x, it.value, rr.value, lat.value, bt.value
+
+    def stats(self) -> dict:
+        v = [C.c_uint64() for _ in range(5)]
+        c = C.c_int32()
+        check(lib().uaamg_server_stats(self._s, *[C.byref(x) for x in v], C.byref(c)),
+              "uaamg_server_stats")
+        keys = ("done", "batches", "cache_hits", "setups", "rejected")
+        out = {k: x.value for k, x in zip(keys, v)}
+        out["cached"] = c.value
+        return out
+
+    def close(self):
+        if self._s:
+            lib().uaamg_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        self.close()

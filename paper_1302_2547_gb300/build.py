@@ -36,12 +36,12 @@ def _needs(obj: str, deps: list[str]) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "uaamg.h")]
     nvcc = _nvcc()
     jobs = []
     for s in srcs:
-        obj = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        obj = os.path.join(BUILD, os.path.splitext(os.path.basename(s))[0] + ".o")
         if force or _needs(obj, [s] + headers):
             jobs.append((s, obj))
 
@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         for msg in ex.map(run, jobs):
             if verbose and msg:
                 print(msg, file=sys.stderr)
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(BUILD, os.path.splitext(os.path.basename(s))[0] + ".o") for s in srcs]
     if force or jobs or _needs(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs]

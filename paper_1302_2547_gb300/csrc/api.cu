@@ -12,6 +12,8 @@ int build_hierarchy(Handle* h, const uaamg_csr* A);
 int solve(Handle* h, const double* b, double* x, double tol, int use_guess, int* iters,
           double* relres);
 int apply_operator(Handle* h, int which, int l, const double* in, double* out);
+int solve_many(Handle* h, int R, const double* B, double* X, double tol, int* iters,
+               double* relres);
 double profile_bytes(const Handle* h);
 
 // Makes the handle's device current for the duration of a call and restores the caller's.
@@ -45,6 +47,8 @@ static void destroy(Handle* h) {
     if (!h) return;
     if (h->work) cudaStreamSynchronize(h->work);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->mgraph) cudaGraphExecDestroy(h->mgraph);
+    if (h->mos_host) cudaFreeHost(h->mos_host);
     for (auto& ps : h->prof_slots) {
         cudaEventDestroy(ps.a);
         cudaEventDestroy(ps.b);
@@ -99,7 +103,7 @@ void uaamg_default_params(uaamg_params* p) {
     p->agg_repeat = 1;
     p->kcycle_ratio = 0.0;
     p->min_coarsening = 0.0;
-    p->fuse_below = kTailMaxN;
+    p->fuse_below = 0;
 }
 
 int uaamg_setup(const uaamg_csr* A, const uaamg_params* p, void* stream, uaamg_handle** out) {
@@ -171,6 +175,25 @@ int uaamg_solve(uaamg_handle* hh, const double* b, double* x, double tol, int32_
     int st = solve(h, b, x, tol, use_guess, &it, &rr);
     *iters = it;
     *relres = rr;
+    leave(h);
+    return st;
+}
+
+int uaamg_solve_many(uaamg_handle* hh, int32_t nrhs, const double* B, double* X, double tol,
+                     int32_t* iters, double* relres) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !B || !X || !iters || !relres || nrhs < 1 || !(tol >= 0.0))
+        return UAAMG_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return UAAMG_ERR_CUDA;
+    enter(h);
+    std::vector<int> it(nrhs, 0);
+    std::vector<double> rr(nrhs, 0.0);
+    int st = solve_many(h, nrhs, B, X, tol, it.data(), rr.data());
+    for (int r = 0; r < nrhs; r++) {
+        iters[r] = it[r];
+        relres[r] = rr[r];
+    }
     leave(h);
     return st;
 }

@@ -92,7 +92,13 @@ struct TailLevel {
     void *rhs, *out, *w, *s, *c1, *v1, *rt, *c2, *v2;
 };
 
-constexpr int kTailMaxN = 8192;  // default size below which levels run fused in one block
+constexpr int kTailMaxN = 8192;  // levels at most this large may run fused in one block
+
+// R-column workspace of one level for uaamg_solve_many (interleaved [n][R]).
+struct MultiLevel {
+    void *rhs, *out, *w, *s, *c1, *v1, *rt, *c2, *v2;
+    double* sc;  // per-column K-cycle scalars, 7 rows of R
+};
 
 struct ProfSlot {
     cudaEvent_t a, b;
@@ -119,6 +125,15 @@ struct Handle {
     // fused small-level K-cycle: first level handled by k_tail (0 = none)
     int tail_level = 0;
     TailLevel* tail_dev = nullptr;
+    // uaamg_solve_many workspace (sized for multi_R columns) and its iteration graph
+    int multi_R = 0;
+    MultiLevel mlev[kMaxLevels];
+    double *mb = nullptr, *mx = nullptr, *mr = nullptr, *mp = nullptr, *mq = nullptr;
+    double* mos = nullptr;       // per-column outer scalars, 8 rows of R
+    double* mos_host = nullptr;  // pinned mirror
+    cudaGraphExec_t mgraph = nullptr;
+    int mgraph_R = 0;
+    long long mgraph_nodes = 0;
     // graph of one outer iteration
     cudaGraphExec_t graph = nullptr;
     long long graph_nodes = 0;
@@ -255,5 +270,8 @@ __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+// a * b + c with one rounding (one FP64 instruction instead of two on GB300's FP64 units)
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 }  // namespace uaamg

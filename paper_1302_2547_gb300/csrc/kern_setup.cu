@@ -169,6 +169,70 @@ __global__ void __launch_bounds__(kThreads) k_paa(PaaArgs a) {
     }
     if (!grid_barrier(a.ctrl)) return;
     int slot = 0, pass = 0;
+    if (a.mode == UAAMG_PASS_SINGLE_ROUND) {
+        // One round per pass (Algorithm 2 as printed), two sweeps and two grid barriers per
+        // pass: (1) b1 and the count of unprocessed vertices; (2) every local maximum becomes
+        // a root and takes its neighbours at once.  Fusing selection and aggregation is safe:
+        // a neighbour w of a root v is never a root itself (P_v > P_w within distance 2) and
+        // no other root reaches it (roots are >= 3 apart), so w has a single writer, and w's
+        // own thread selects nothing whether it reads w's old or new state.
+        while (true) {
+            int cnt = 0;
+            for (int v = g0; v < a.n; v += gs) {
+                const int k0 = a.rowptr[v], k1 = a.rowptr[v + 1];
+                uint64_t best = 0;
+                for (int k = k0; k < k1; k++) {
+                    const int u = a.col[k];
+                    if (ld_state(a.state + u) == ST_CAND) {
+                        const uint64_t pu = a.prio[u];
+                        best = pu > best ? pu : best;
+                    }
+                }
+                a.b1[v] = best;
+                cnt += (ld_state(a.state + v) == ST_CAND);
+            }
+            cnt = block_sum_int(cnt);
+            if (threadIdx.x == 0 && cnt) atomicAdd(&a.slots[slot], cnt);
+            if (!grid_barrier(a.ctrl)) return;
+            const int remaining = *(volatile int*)&a.slots[slot];
+            slot++;
+            if (remaining == 0) break;
+            if (slot >= a.nslots) {
+                if (g0 == 0) atomicOr(&a.ctrl->err, kErrSlots);
+                return;
+            }
+            for (int v = g0; v < a.n; v += gs) {
+                if (ld_state(a.state + v) != ST_CAND) continue;
+                const int k0 = a.rowptr[v], k1 = a.rowptr[v + 1];
+                uint64_t m = 0;
+                for (int k = k0; k < k1; k++) {
+                    const uint64_t bu = __ldcg(reinterpret_cast<const unsigned long long*>(a.b1 + a.col[k]));
+                    m = bu > m ? bu : m;
+                }
+                if (m != a.prio[v]) continue;
+                int taken = 1;  // v is a root: its star aggregate
+                for (int k = k0; k < k1; k++) {
+                    const int u = a.col[k];
+                    if (u == v) continue;
+                    if (a.t > 0 && taken >= a.t) break;
+                    if (ld_state(a.state + u) == ST_CAND) {
+                        a.root_of[u] = v;
+                        a.pass_of[u] = pass;
+                        a.state[u] = ST_DONE;
+                        taken++;
+                    }
+                }
+                a.root_of[v] = v;
+                a.pass_of[v] = pass;
+                a.agg_size[v] = taken;
+                a.state[v] = ST_DONE;
+            }
+            if (!grid_barrier(a.ctrl)) return;
+            pass++;
+        }
+        if (g0 == 0) a.ctrl->npasses = pass;
+        return;
+    }
     while (true) {
         // (A) coarse vertices of this pass
         while (true) {
@@ -591,17 +655,24 @@ k_dense_gather(int n, const int* __restrict__ rowptr, const int* __restrict__ co
     for (int k = rowptr[i]; k < rowptr[i + 1]; k++) D[(size_t)i * n + col[k]] = val[k];
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_chol_inverse(int n, double* __restrict__ D, double* __restrict__ X, Ctrl* ctrl) {
+// Left-looking Cholesky in one block: for column j, warp w computes the dot products of
+// rows i = j + w, j + w + 32, ... with row j over k < j (lanes over k), first the diagonal.
+__global__ void __launch_bounds__(1024)
+k_chol_factor(int n, double* __restrict__ D, Ctrl* ctrl) {
     __shared__ int bad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     for (int j = 0; j < n; j++) {
-        if (threadIdx.x == 0) {
-            double s = D[(size_t)j * n + j];
-            for (int k = 0; k < j; k++) s -= D[(size_t)j * n + k] * D[(size_t)j * n + k];
-            if (!(s > 0.0)) bad = 1;
-            else D[(size_t)j * n + j] = sqrt(s);
+        if (warp == 0) {
+            double s = 0.0;
+            for (int k = lane; k < j; k += 32) s += D[(size_t)j * n + k] * D[(size_t)j * n + k];
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double d = D[(size_t)j * n + j] - s;
+                if (!(d > 0.0)) bad = 1;
+                else D[(size_t)j * n + j] = sqrt(d);
+            }
         }
         __syncthreads();
         if (bad) {
@@ -609,33 +680,48 @@ k_chol_inverse(int n, double* __restrict__ D, double* __restrict__ X, Ctrl* ctrl
             return;
         }
         const double ljj = D[(size_t)j * n + j];
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-            double v = D[(size_t)i * n + j];
-            for (int k = 0; k < j; k++) v -= D[(size_t)i * n + k] * D[(size_t)j * n + k];
-            D[(size_t)i * n + j] = v / ljj;
+        for (int i = j + 1 + warp; i < n; i += nw) {
+            double s = 0.0;
+            for (int k = lane; k < j; k += 32) s += D[(size_t)i * n + k] * D[(size_t)j * n + k];
+            s = warp_sum(s);
+            if (lane == 0) D[(size_t)i * n + j] = (D[(size_t)i * n + j] - s) / ljj;
         }
         __syncthreads();
     }
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        for (int i = 0; i < n; i++) {  // L y = e_c
-            double v = (i == c) ? 1.0 : 0.0;
-            for (int k = 0; k < i; k++) v -= D[(size_t)i * n + k] * X[(size_t)k * n + c];
-            X[(size_t)i * n + c] = v / D[(size_t)i * n + i];
-        }
-        for (int i = n - 1; i >= 0; i--) {  // L^T x = y
-            double v = X[(size_t)i * n + c];
-            for (int k = i + 1; k < n; k++) v -= D[(size_t)k * n + i] * X[(size_t)k * n + c];
-            X[(size_t)i * n + c] = v / D[(size_t)i * n + i];
-        }
+}
+
+// Column c of the inverse, one warp per column: L y = e_c forward, then L^T x = y backward,
+// each step a warp-parallel dot product; y lives in shared memory.
+__global__ void __launch_bounds__(32)
+k_chol_inverse_cols(int n, const double* __restrict__ L, double* __restrict__ X) {
+    __shared__ double y[kMaxCoarsest];
+    const int c = blockIdx.x, lane = threadIdx.x;
+    for (int i = lane; i < n; i += 32) y[i] = 0.0;
+    __syncwarp();
+    for (int i = c; i < n; i++) {
+        double s = 0.0;
+        for (int k = c + lane; k < i; k += 32) s += L[(size_t)i * n + k] * y[k];
+        s = warp_sum(s);
+        if (lane == 0) y[i] = ((i == c ? 1.0 : 0.0) - s) / L[(size_t)i * n + i];
+        __syncwarp();
     }
+    for (int i = n - 1; i >= 0; i--) {
+        double s = 0.0;
+        for (int k = i + 1 + lane; k < n; k += 32) s += L[(size_t)k * n + i] * y[k];
+        s = warp_sum(s);
+        if (lane == 0) y[i] = (y[i] - s) / L[(size_t)i * n + i];
+        __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) X[(size_t)i * n + c] = y[i];
 }
 
 int launch_dense_coarsest(Handle* h, int n, const int* rowptr, const int* col,
                           const double* val, double* work, double* inv) {
     cudaMemsetAsync(work, 0, sizeof(double) * (size_t)n * n, h->work);
     k_dense_gather<<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, rowptr, col, val, work);
-    k_chol_inverse<<<1, kThreads, 0, h->work>>>(n, work, inv, h->ctrl);
-    count_launch(h, 2);
+    k_chol_factor<<<1, 1024, 0, h->work>>>(n, work, h->ctrl);
+    k_chol_inverse_cols<<<n, 32, 0, h->work>>>(n, work, inv);
+    count_launch(h, 3);
     return check_cuda(cudaGetLastError());
 }
 

@@ -3,10 +3,11 @@
 // (Section 4.2), the scalar steps of the K-cycle (Section 4.3) and of the outer flexible CG.
 //
 // Row-block SpMV: a block owns 256 consecutive rows.  Their entries form one contiguous
-// range of col/val, which the block streams in chunks with coalesced loads, multiplying
-// each value by the gathered vector entry into shared memory; each thread then adds its
-// own row's products in stored order and applies the fused epilogue.  Loads are therefore
-// coalesced whatever the row lengths, and every row sum has a fixed order.
+// range of col/val, which the block streams in chunks with coalesced 16-byte loads, storing
+// each value and the gathered vector entry in shared memory; each thread then accumulates
+// its own row in stored order with fused multiply-adds and applies the fused epilogue.
+// Loads are therefore coalesced whatever the row lengths, and every row sum has a fixed
+// order.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -44,7 +45,8 @@ __device__ __forceinline__ void ld_val4(const double* p, double (&v)[4]) {
 template <typename T, int MODE, int ND>
 __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
     if (a.skip && *(volatile const int*)a.skip) return;
-    __shared__ T prod[kChunk];
+    __shared__ T sval[kChunk];
+    __shared__ T sx[kChunk];
     const int r0 = blockIdx.x * kRowsPerBlock;
     const int r1 = min(a.n, r0 + kRowsPerBlock);
     const int row = r0 + threadIdx.x;
@@ -81,12 +83,15 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 const int k = kb + e;
-                if (k >= c0 && k < c1) prod[k - c0] = mul_rn(v[e], rb_gather<T, MODE>(a, j[e]));
+                if (k >= c0 && k < c1) {
+                    sval[k - c0] = v[e];
+                    sx[k - c0] = rb_gather<T, MODE>(a, j[e]);
+                }
             }
         }
         __syncthreads();
         const int lo = max(rs, c0), hi = min(re, c1);
-        for (int k = lo; k < hi; k++) acc = add_rn(acc, prod[k - c0]);
+        for (int k = lo; k < hi; k++) acc = fma_rn(sval[k - c0], sx[k - c0], acc);
         __syncthreads();
     }
     double dv[ND > 0 ? ND : 1];

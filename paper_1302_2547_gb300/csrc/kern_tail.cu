@@ -56,7 +56,7 @@ __device__ __forceinline__ void spmv_rows(const TailLevel& L, const T* x, T* y, 
     for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
         T acc = T(0);
         for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; k++)
-            acc = add_rn(acc, mul_rn(val[k], x[L.col[k]]));
+            acc = fma_rn(val[k], x[L.col[k]], acc);
         y[i] = acc;
         const double xi = (double)x[i];
         d[0] += xi * (double)acc;
@@ -164,7 +164,7 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
                     T acc = T(0);
                     for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; k++) {
                         const int j = L.col[k];
-                        acc = add_rn(acc, mul_rn(val[k], mul_rn(minv[j], in[j])));
+                        acc = fma_rn(val[k], mul_rn(minv[j], in[j]), acc);
                     }
                     x[i] = mul_rn(minv[i], in[i]);
                     s[i] = sub_rn(in[i], acc);
@@ -184,7 +184,7 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
                     T acc = T(0);
                     for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; k++) {
                         const int j = L.col[k];
-                        acc = add_rn(acc, mul_rn(val[k], add_rn(x[j], ec[L.agg[j]])));
+                        acc = fma_rn(val[k], add_rn(x[j], ec[L.agg[j]]), acc);
                     }
                     const T xi = add_rn(x[i], ec[L.agg[i]]);
                     out[i] = add_rn(xi, mul_rn(minv[i], sub_rn(in[i], acc)));

@@ -99,6 +99,46 @@ int launch_prolong(Handle* h, int n, const T* x, const int* agg, const T* e, T* 
 template <typename T>
 int launch_tail(Handle* h, int m0);
 
+// R right-hand sides at once (kern_multi.cu)
+template <typename T>
+struct MArgs {
+    int n, R;
+    const int* rowptr;
+    const int* col;
+    const T* val;
+    const T* minv;
+    const T* r;
+    const T* x;
+    const int* agg;
+    const T* e;
+    T* y;
+    T* y2;
+    const T* d1;
+    const T* d2;
+    double* partials;
+    unsigned int* counter;
+    double* result;
+};
+template <typename T>
+int launch_mrow(Handle* h, int mode, int ndots, const MArgs<T>& a);
+template <typename T>
+int launch_mrestrict(Handle* h, int nc, int R, const int* aggptr, const int* members,
+                     const T* s, T* rc);
+template <typename T>
+int launch_mdense(Handle* h, int n, int R, const double* inv, const T* in, T* out);
+template <typename T>
+int launch_mkc_rt(Handle* h, int n, int R, const T* rho, const T* v1, T* rt, double* sc,
+                  bool tau);
+template <typename T>
+int launch_mkc_combine(Handle* h, int n, int R, const T* c1, const T* c2, T* e,
+                       const double* sc, int second, double tau);
+int launch_mcast(Handle* h, long long m, const double* in, float* out);
+template <typename T>
+int launch_mouter(Handle* h, int n, int R, const T* z, double* p, const double* q, double* os);
+int launch_mxr(Handle* h, int n, int R, double* x, double* r, const double* p, const double* q,
+               double* os);
+int launch_mnorm(Handle* h, int n, int R, const double* b, double* out);
+
 // outer flexible CG (FP64 with the preconditioner output in T)
 int launch_cast_d2f(Handle* h, int n, const double* in, float* out);
 template <typename T>

@@ -1,0 +1,341 @@
+// server.cpp -- a solve service on one GPU: requests (matrix, right-hand side, tolerance)
+// are queued, admitted against a device-memory budget, served from a cache of device-
+// resident hierarchies keyed by the matrix, and batched: queued requests for the same
+// matrix are solved together with uaamg_solve_many, and worker threads with their own
+// CUDA streams keep several solves in flight.  Host-side orchestration only: every compute
+// step is a libuaamg kernel.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "uaamg.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Matrix {
+    uint64_t key = 0;
+    int32_t n = 0, nnz = 0;
+    std::vector<int32_t> rowptr, col;
+    std::vector<double> val;
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    std::shared_ptr<Matrix> A;
+    std::vector<double> b;
+    double tol = 1e-8;
+    Clock::time_point t_submit;
+    // result
+    std::vector<double> x;
+    int32_t status = -1, iters = 0, batch = 0, cache_hit = 0;
+    double relres = 0.0, latency_ms = 0.0;
+    bool done = false;
+};
+
+struct CacheEntry {
+    uint64_t key;
+    uaamg_handle* h = nullptr;
+    uint64_t bytes = 0;
+    int users = 0;  // workers currently solving with it
+    cudaStream_t stream = nullptr;
+};
+
+// 64-bit FNV-1a over the CSR arrays: the cache key of a matrix when the caller gives none.
+uint64_t fnv1a(const void* p, size_t bytes, uint64_t h) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < bytes; i++) {
+        h ^= c[i];
+        h *= 0x100000001b3ULL;
+    }
+    return h;
+}
+
+}  // namespace
+
+struct uaamg_server {
+    uaamg_params params{};
+    uint64_t budget = 0;
+    int max_batch = 16;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> tickets;
+    std::list<CacheEntry> cache;  // most recently used first
+    std::vector<std::thread> workers;
+    uint64_t next_ticket = 1;
+    bool stopping = false;
+    int device = 0;
+    // statistics
+    uint64_t n_done = 0, n_batches = 0, n_hits = 0, n_setups = 0, n_rejected = 0;
+
+    CacheEntry* find(uint64_t key) {
+        for (auto it = cache.begin(); it != cache.end(); ++it)
+            if (it->key == key) {
+                cache.splice(cache.begin(), cache, it);
+                return &cache.front();
+            }
+        return nullptr;
+    }
+    // Evicts least recently used idle hierarchies until `need` more bytes fit the budget.
+    bool make_room(uint64_t need) {
+        if (!budget) return true;
+        while (uaamg_memory_in_use() + need > budget) {
+            auto victim = cache.end();
+            for (auto it = cache.begin(); it != cache.end(); ++it)
+                if (it->users == 0) victim = it;
+            if (victim == cache.end()) return false;
+            uaamg_free(victim->h);
+            if (victim->stream) cudaStreamDestroy(victim->stream);
+            cache.erase(victim);
+        }
+        return true;
+    }
+    void worker_main(int wid);
+};
+
+// Device bytes a hierarchy of this matrix may take (level 0 plus coarse levels, smoother
+// data, workspace and setup scratch): used for admission before setup runs.
+static uint64_t estimate_bytes(const Matrix& A, int max_batch) {
+    const uint64_t n = (uint64_t)A.n, z = (uint64_t)A.nnz;
+    return 2 * (16 * z + 120 * n) + (uint64_t)max_batch * n * 48 + (64ULL << 20);
+}
+
+void uaamg_server::worker_main(int wid) {
+    cudaSetDevice(device);
+    cudaStream_t stream = nullptr;
+    cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    while (true) {
+        std::vector<std::shared_ptr<Request>> batch;
+        CacheEntry* entry = nullptr;
+        bool need_setup = false;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
+            if (stopping && queue.empty()) break;
+            // continuous batching: the oldest request plus every queued request for the same
+            // matrix and tolerance, up to max_batch
+            auto first = queue.front();
+            queue.pop_front();
+            batch.push_back(first);
+            for (auto it = queue.begin(); it != queue.end() && (int)batch.size() < max_batch;) {
+                if ((*it)->A->key == first->A->key && (*it)->tol == first->tol) {
+                    batch.push_back(*it);
+                    it = queue.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            entry = find(first->A->key);
+            if (entry) {
+                entry->users++;
+                n_hits += batch.size();
+                for (auto& r : batch) r->cache_hit = 1;
+            } else {
+                const uint64_t need = estimate_bytes(*first->A, max_batch);
+                if (budget && need > budget) {  // can never fit: reject
+                    for (auto& r : batch) {
+                        r->status = UAAMG_ERR_BUDGET;
+                        r->done = true;
+                    }
+                    n_rejected += batch.size();
+                    cv_done.notify_all();
+                    continue;
+                }
+                if (!make_room(need)) {  // wait for memory: put the batch back at the front
+                    for (auto it = batch.rbegin(); it != batch.rend(); ++it) queue.push_front(*it);
+                    cv_done.wait_for(lk, std::chrono::milliseconds(2));
+                    continue;
+                }
+                cache.push_front(CacheEntry{first->A->key, nullptr, need, 1, nullptr});
+                entry = &cache.front();
+                need_setup = true;
+            }
+        }
+        const Matrix& A = *batch[0]->A;
+        int st = UAAMG_OK;
+        if (need_setup) {
+            uaamg_csr csr{A.n, A.nnz, A.rowptr.data(), A.col.data(), A.val.data(), 0};
+            uaamg_handle* h = nullptr;
+            st = uaamg_setup(&csr, &params, stream, &h);
+            std::lock_guard<std::mutex> lk(mu);
+            n_setups++;
+            if (st != UAAMG_OK) {
+                for (auto it = cache.begin(); it != cache.end(); ++it)
+                    if (&*it == entry) {
+                        cache.erase(it);
+                        break;
+                    }
+                entry = nullptr;
+            } else {
+                entry->h = h;
+            }
+        }
+        const int R = (int)batch.size();
+        std::vector<int32_t> its(R, 0);
+        std::vector<double> rr(R, 0.0);
+        std::vector<double> X((size_t)A.n * R, 0.0);
+        if (st == UAAMG_OK) {
+            if (R == 1) {
+                st = uaamg_solve(entry->h, batch[0]->b.data(), X.data(), batch[0]->tol, 0, &its[0],
+                                 &rr[0]);
+            } else {
+                std::vector<double> B((size_t)A.n * R);
+                for (int r = 0; r < R; r++)
+                    for (int i = 0; i < A.n; i++) B[(size_t)i * R + r] = batch[r]->b[i];
+                st = uaamg_solve_many(entry->h, R, B.data(), X.data(), batch[0]->tol, its.data(),
+                                      rr.data());
+            }
+        }
+        const auto t_end = Clock::now();
+        std::lock_guard<std::mutex> lk(mu);
+        if (entry) entry->users--;
+        for (int r = 0; r < R; r++) {
+            Request& q = *batch[r];
+            q.x.resize(A.n);
+            for (int i = 0; i < A.n; i++) q.x[i] = X[(size_t)i * R + r];
+            q.status = (st == UAAMG_ERR_NO_CONVERGENCE) ? (rr[r] <= q.tol ? UAAMG_OK : st) : st;
+            q.iters = its[r];
+            q.relres = rr[r];
+            q.batch = R;
+            q.latency_ms = std::chrono::duration<double, std::milli>(t_end - q.t_submit).count();
+            q.done = true;
+        }
+        n_done += R;
+        n_batches++;
+        cv_done.notify_all();
+    }
+    cudaStreamDestroy(stream);
+}
+
+extern "C" {
+
+int uaamg_server_create(const uaamg_params* p, uint64_t budget_bytes, int32_t workers,
+                        int32_t max_batch, uaamg_server** out) {
+    if (!out || workers < 1 || workers > 64 || max_batch < 1 || max_batch > 32)
+        return UAAMG_ERR_INVALID_ARG;
+    *out = nullptr;
+    uaamg_server* s = new uaamg_server();
+    if (p) s->params = *p;
+    else uaamg_default_params(&s->params);
+    s->budget = budget_bytes;
+    s->max_batch = max_batch;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return UAAMG_ERR_CUDA;
+    }
+    if (budget_bytes) uaamg_set_memory_budget(budget_bytes);
+    for (int w = 0; w < workers; w++) s->workers.emplace_back(&uaamg_server::worker_main, s, w);
+    *out = s;
+    return UAAMG_OK;
+}
+
+int uaamg_server_submit(uaamg_server* s, const uaamg_csr* A, uint64_t matrix_key,
+                        const double* b, double tol, uint64_t* ticket) {
+    if (!s || !A || !b || !ticket || A->on_device || A->n < 1 || A->nnz < A->n || !(tol >= 0.0))
+        return UAAMG_ERR_INVALID_ARG;
+    auto req = std::make_shared<Request>();
+    req->t_submit = Clock::now();
+    uint64_t key = matrix_key;
+    if (!key) {
+        key = 0xcbf29ce484222325ULL;
+        key = fnv1a(&A->n, sizeof(A->n), key);
+        key = fnv1a(A->rowptr, sizeof(int32_t) * ((size_t)A->n + 1), key);
+        key = fnv1a(A->col, sizeof(int32_t) * (size_t)A->nnz, key);
+        key = fnv1a(A->val, sizeof(double) * (size_t)A->nnz, key);
+    }
+    std::shared_ptr<Matrix> M;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto& q : s->queue)
+            if (q->A->key == key) M = q->A;
+    }
+    if (!M) {
+        M = std::make_shared<Matrix>();
+        M->key = key;
+        M->n = A->n;
+        M->nnz = A->nnz;
+        M->rowptr.assign(A->rowptr, A->rowptr + A->n + 1);
+        M->col.assign(A->col, A->col + A->nnz);
+        M->val.assign(A->val, A->val + A->nnz);
+    }
+    req->A = M;
+    req->b.assign(b, b + A->n);
+    req->tol = tol;
+    std::lock_guard<std::mutex> lk(s->mu);
+    req->ticket = s->next_ticket++;
+    *ticket = req->ticket;
+    s->tickets[req->ticket] = req;
+    s->queue.push_back(req);
+    s->cv_work.notify_one();
+    return UAAMG_OK;
+}
+
+int uaamg_server_poll(uaamg_server* s, uint64_t ticket, int32_t* done) {
+    if (!s || !done) return UAAMG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return UAAMG_ERR_INVALID_ARG;
+    *done = it->second->done ? 1 : 0;
+    return UAAMG_OK;
+}
+
+int uaamg_server_wait(uaamg_server* s, uint64_t ticket, double* x, int32_t* iters,
+                      double* relres, double* latency_ms, int32_t* batch) {
+    if (!s) return UAAMG_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return UAAMG_ERR_INVALID_ARG;
+    std::shared_ptr<Request> req = it->second;
+    s->cv_done.wait(lk, [&] { return req->done; });
+    if (x && !req->x.empty()) memcpy(x, req->x.data(), sizeof(double) * req->x.size());
+    if (iters) *iters = req->iters;
+    if (relres) *relres = req->relres;
+    if (latency_ms) *latency_ms = req->latency_ms;
+    if (batch) *batch = req->batch;
+    s->tickets.erase(it);
+    return req->status;
+}
+
+int uaamg_server_stats(uaamg_server* s, uint64_t* done, uint64_t* batches, uint64_t* cache_hits,
+                       uint64_t* setups, uint64_t* rejected, int32_t* cached) {
+    if (!s) return UAAMG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (done) *done = s->n_done;
+    if (batches) *batches = s->n_batches;
+    if (cache_hits) *cache_hits = s->n_hits;
+    if (setups) *setups = s->n_setups;
+    if (rejected) *rejected = s->n_rejected;
+    if (cached) *cached = (int32_t)s->cache.size();
+    return UAAMG_OK;
+}
+
+void uaamg_server_destroy(uaamg_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->workers) t.join();
+    for (auto& e : s->cache) {
+        if (e.h) uaamg_free(e.h);
+    }
+    s->cache.clear();
+    if (s->budget) uaamg_set_memory_budget(0);
+    delete s;
+}
+
+}  // extern "C"

