@@ -128,11 +128,13 @@ def workload():
 
 
 EAGER = False  # --eager: launch every kernel directly instead of replaying graphs
+TMA_ROWS = None  # --tma-rows: levels of at least this many rows use the TMA-staged kernels
 
 
 def bench_params(U, precision, profile_class=0):
+    extra = {} if TMA_ROWS is None else {"tma_rows": TMA_ROWS}
     return U.uaamg_default_params(precision=precision, profile_class=profile_class,
-                                  use_graphs=0 if EAGER else 1, **BENCH_PARAMS)
+                                  use_graphs=0 if EAGER else 1, **BENCH_PARAMS, **extra)
 
 
 def run_gpu(args, rank, world):
@@ -313,6 +315,7 @@ def run_gpu(args, rank, world):
         "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "tol": TOL,
                    "precision": "FP32 hierarchy + K-cycle, FP64 outer flexible CG",
                    **BENCH_PARAMS, "pass_mode": "single round (Algorithm 2)",
+                   "tma_rows": bench_params(U, U.UAAMG_MIXED).tma_rows,
                    "l2": "inputs larger than L2 (CSR 183 MB FP64 > 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "setup_ms": round(float(np.median([r[2]['setup_ms'] for r in rec])), 3),
@@ -366,9 +369,12 @@ def main():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-plain", action="store_true", help="do not time the FP64 path")
     ap.add_argument("--skip-batched", action="store_true", help="do not time solve_many")
+    ap.add_argument("--tma-rows", type=int, default=None,
+                    help="row threshold of the TMA-staged row-block kernels (0 = off)")
     args = ap.parse_args()
-    global EAGER
+    global EAGER, TMA_ROWS
     EAGER = args.eager
+    TMA_ROWS = args.tma_rows
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
 

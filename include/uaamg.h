@@ -86,6 +86,13 @@ typedef struct uaamg_params {
                              n_{m-1} / n_m >= kcycle_ratio; default 0 (always two steps) */
     double min_coarsening; /* > 0: a level of at most 1024 unknowns whose aggregation would
                               shrink it by less than this factor becomes the coarsest; 0 */
+    double jacobi_omega;  /* 0 (default): l1-Jacobi smoother; > 0: damped Jacobi
+                             x += omega D^{-1} (b - A x) (Section 4.1) */
+    int32_t tma_rows;     /* levels with at least this many rows run their SpMV-based kernels
+                             as persistent blocks that stream the matrix into shared memory
+                             with TMA bulk copies, one thread per row (0 = never); default
+                             262144.  Changes no vector entry; fused inner products are summed
+                             in another fixed order. */
     int32_t fuse_below;   /* coarse levels with at most this many unknowns run their K-cycle
                              in one fused single-block kernel (pre = post = 1 only); 0 = off
                              (default: on GB300 one block is slower than launching) */
@@ -177,7 +184,7 @@ int uaamg_get_stats(const uaamg_handle* h, uaamg_stats* s);
  * launch of the selected kernel class is bracketed by CUDA events on the launching stream
  * (inside the captured graphs as well), and the durations accumulate.
  */
-#define UAAMG_KCLASS_SMOOTH0 1  /* level-0 fused SpMV + l1-Jacobi kernels of the K-cycle */
+#define UAAMG_KCLASS_SMOOTH0 1  /* level-0 first l1-Jacobi sweep + residual (fused SpMV) */
 #define UAAMG_KCLASS_SPMV64 2   /* level-0 FP64 SpMV + dot kernel of the outer iteration */
 #define UAAMG_KCLASS_PAA 3      /* the aggregation kernel of setup level 0 */
 #define UAAMG_KCLASS_COARSE 4   /* the coarse-operator assembly kernel of setup level 0 */

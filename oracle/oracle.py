@@ -39,7 +39,8 @@ class _Params(C.Structure):
                 ("max_agg_size", C.c_int32), ("pass_mode", C.c_int32), ("seed", C.c_uint64),
                 ("pre", C.c_int32), ("post", C.c_int32), ("kcycle_inner", C.c_int32),
                 ("kcycle_tau", C.c_double), ("max_iter", C.c_int32), ("agg_repeat", C.c_int32),
-                ("kcycle_ratio", C.c_double), ("min_coarsening", C.c_double)]
+                ("kcycle_ratio", C.c_double), ("min_coarsening", C.c_double),
+                ("jacobi_omega", C.c_double)]
 
 
 _lib = None
@@ -180,11 +181,13 @@ class Params:
     agg_repeat: int = 1
     kcycle_ratio: float = 0.0
     min_coarsening: float = 0.0
+    jacobi_omega: float = 0.0
 
     def c(self) -> _Params:
         return _Params(self.coarse_size, self.max_levels, self.max_agg_size, self.pass_mode,
                        self.seed, self.pre, self.post, self.kcycle_inner, self.kcycle_tau,
-                       self.max_iter, self.agg_repeat, self.kcycle_ratio, self.min_coarsening)
+                       self.max_iter, self.agg_repeat, self.kcycle_ratio, self.min_coarsening,
+                       self.jacobi_omega)
 
 
 class Hierarchy:

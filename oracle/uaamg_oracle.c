@@ -271,6 +271,17 @@ int64_t or_coarse(int32_t n, const int32_t* rowptr, const int32_t* col, const do
 /* l1-Jacobi smoother, Section 4.1                                                       */
 /* ------------------------------------------------------------------------------------ */
 
+/* Damped Jacobi (Section 4.1): Minv_i = omega / a_ii. */
+void or_minv_damped(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                    double omega, double* minv) {
+    for (int32_t i = 0; i < n; i++) {
+        double diag = 0.0;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; k++)
+            if (col[k] == i) diag = val[k];
+        minv[i] = omega / diag;
+    }
+}
+
 /* Minv_i = 1 / (a_ii + sum_{j != i} |a_ij|), the row sum taken in stored order. */
 void or_minv(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
              double* minv) {
@@ -338,6 +349,7 @@ typedef struct or_params {
     double kcycle_ratio;  /* > 0: level m takes its second step only if n_{m-1}/n_m >= this */
     double min_coarsening; /* > 0: a level with n <= 1024 that would shrink by less than this
                               factor becomes the coarsest */
+    double jacobi_omega;  /* 0: l1-Jacobi; > 0: damped Jacobi x += omega D^{-1} (b - A x) */
 } or_params;
 
 typedef struct or_level {
@@ -365,7 +377,8 @@ void* or_setup(int32_t n, const int32_t* rowptr, const int32_t* col, const doubl
     if (n < 1 || p->coarse_size < 1 || p->max_levels < 1 || p->max_levels > OR_MAX_LEVELS ||
         p->max_agg_size < 0 || p->max_agg_size == 1 || p->pre < 0 || p->post < 0 ||
         p->kcycle_inner < 1 || p->kcycle_inner > 2 || p->max_iter < 0 ||
-        p->agg_repeat < 1 || p->agg_repeat > 2 || p->kcycle_ratio < 0 || p->min_coarsening < 0)
+        p->agg_repeat < 1 || p->agg_repeat > 2 || p->kcycle_ratio < 0 || p->min_coarsening < 0 ||
+        p->jacobi_omega < 0)
         return NULL;
     or_hier* h = (or_hier*)calloc(1, sizeof(or_hier));
     h->p = *p;
@@ -462,7 +475,10 @@ void* or_setup(int32_t n, const int32_t* rowptr, const int32_t* col, const doubl
     for (int32_t q = 0; q < h->nlev; q++) {
         or_level* Lq = &h->lev[q];
         Lq->minv = (double*)malloc(sizeof(double) * (size_t)Lq->n);
-        or_minv(Lq->n, Lq->rowptr, Lq->col, Lq->val, Lq->minv);
+        if (p->jacobi_omega > 0.0)
+            or_minv_damped(Lq->n, Lq->rowptr, Lq->col, Lq->val, p->jacobi_omega, Lq->minv);
+        else
+            or_minv(Lq->n, Lq->rowptr, Lq->col, Lq->val, Lq->minv);
     }
     or_level* Lc = &h->lev[h->nlev - 1];
     if (Lc->n > OR_MAX_COARSEST) {

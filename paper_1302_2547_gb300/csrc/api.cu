@@ -75,7 +75,8 @@ static bool params_ok(const uaamg_params* p) {
            (p->precision == UAAMG_FP64 || p->precision == UAAMG_MIXED) && p->max_iter >= 0 &&
            p->profile_class >= 0 && p->profile_class <= UAAMG_KCLASS_COARSE &&
            (p->agg_repeat == 1 || p->agg_repeat == 2) && p->kcycle_ratio >= 0.0 &&
-           p->min_coarsening >= 0.0 && p->fuse_below >= 0;
+           p->min_coarsening >= 0.0 && p->fuse_below >= 0 && p->jacobi_omega >= 0.0 &&
+           p->tma_rows >= 0;
 }
 
 }  // namespace uaamg
@@ -103,6 +104,8 @@ void uaamg_default_params(uaamg_params* p) {
     p->agg_repeat = 1;
     p->kcycle_ratio = 0.0;
     p->min_coarsening = 0.0;
+    p->jacobi_omega = 0.0;
+    p->tma_rows = 262144;
     p->fuse_below = 0;
 }
 

@@ -78,6 +78,7 @@ struct Level {
     int* aggptr = nullptr;   // [nc+1] members of each aggregate, ascending
     int* members = nullptr;  // [n]
     int passes = 0;
+    int rb_rows = kRowsPerBlock;  // rows per block of this level's row-block kernels
     // K-cycle workspace in the handle's precision
     void *rhs = nullptr, *out = nullptr, *w = nullptr, *s = nullptr;
     void *c1 = nullptr, *v1 = nullptr, *rt = nullptr, *c2 = nullptr, *v2 = nullptr;

@@ -325,6 +325,162 @@ __global__ void __launch_bounds__(kThreads) k_paa(PaaArgs a) {
     if (g0 == 0) a.ctrl->npasses = pass;
 }
 
+// The same passes for a small level in one thread block: the vertex states and b1 live in
+// shared memory ("staged in shared memory"), and __syncthreads replaces the grid barriers,
+// which on levels of a few thousand vertices cost more than the sweeps themselves.
+constexpr int kPaaSmallN = 8192;
+constexpr int kPaaSmallThreads = 1024;
+
+__device__ __forceinline__ int block_sum_big(int v, int* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[w];
+    __syncthreads();
+    return s;
+}
+
+__global__ void __launch_bounds__(kPaaSmallThreads, 1) k_paa_small(PaaArgs a) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    uint64_t* b1 = reinterpret_cast<uint64_t*>(dyn);
+    uint8_t* state = dyn + sizeof(uint64_t) * kPaaSmallN;
+    uint8_t* blocked = state + kPaaSmallN;
+    __shared__ int red[kPaaSmallThreads / 32];
+    const int t = threadIdx.x, T = blockDim.x;
+    for (int v = t; v < a.n; v += T) {
+        state[v] = ST_CAND;
+        a.root_of[v] = -1;
+        a.pass_of[v] = -1;
+    }
+    __syncthreads();
+    int pass = 0, rounds = 0;
+    while (true) {
+        if (a.mode == UAAMG_PASS_SINGLE_ROUND) {
+            // sweep 1: b1 and the count of unprocessed vertices
+            int cnt = 0;
+            for (int v = t; v < a.n; v += T) {
+                uint64_t best = 0;
+                for (int k = a.rowptr[v]; k < a.rowptr[v + 1]; k++) {
+                    const int u = a.col[k];
+                    if (state[u] == ST_CAND) {
+                        const uint64_t pu = a.prio[u];
+                        best = pu > best ? pu : best;
+                    }
+                }
+                b1[v] = best;
+                cnt += (state[v] == ST_CAND);
+            }
+            if (block_sum_big(cnt, red) == 0) break;
+            // sweep 2: local maxima become roots and take their neighbours (see k_paa)
+            for (int v = t; v < a.n; v += T) {
+                if (state[v] != ST_CAND) continue;
+                const int k0 = a.rowptr[v], k1 = a.rowptr[v + 1];
+                uint64_t m = 0;
+                for (int k = k0; k < k1; k++) {
+                    const uint64_t bu = b1[a.col[k]];
+                    m = bu > m ? bu : m;
+                }
+                if (m != a.prio[v]) continue;
+                int taken = 1;
+                for (int k = k0; k < k1; k++) {
+                    const int u = a.col[k];
+                    if (u == v) continue;
+                    if (a.t > 0 && taken >= a.t) break;
+                    if (state[u] == ST_CAND) {
+                        a.root_of[u] = v;
+                        a.pass_of[u] = pass;
+                        state[u] = ST_DONE;
+                        taken++;
+                    }
+                }
+                a.root_of[v] = v;
+                a.pass_of[v] = pass;
+                a.agg_size[v] = taken;
+                state[v] = ST_DONE;
+            }
+            __syncthreads();
+        } else {
+            // maximal set per pass: rounds until no candidate remains, then aggregation
+            while (true) {
+                for (int v = t; v < a.n; v += T) {
+                    uint64_t best = 0;
+                    int blk = 0;
+                    for (int k = a.rowptr[v]; k < a.rowptr[v + 1]; k++) {
+                        const int u = a.col[k];
+                        const uint8_t s = state[u];
+                        blk |= (s == ST_ROOT);
+                        if (s == ST_CAND) {
+                            const uint64_t pu = a.prio[u];
+                            best = pu > best ? pu : best;
+                        }
+                    }
+                    b1[v] = best;
+                    blocked[v] = (uint8_t)blk;
+                }
+                __syncthreads();
+                int cnt = 0;
+                for (int v = t; v < a.n; v += T) {
+                    if (state[v] != ST_CAND) continue;
+                    uint64_t m = 0;
+                    int blk = 0;
+                    for (int k = a.rowptr[v]; k < a.rowptr[v + 1]; k++) {
+                        const int u = a.col[k];
+                        blk |= blocked[u];
+                        m = b1[u] > m ? b1[u] : m;
+                    }
+                    if (blk) state[v] = ST_EXCL;
+                    else if (m == a.prio[v]) state[v] = ST_ROOT;
+                    else cnt++;
+                }
+                const int remaining = block_sum_big(cnt, red);
+                if (++rounds >= a.nslots) {
+                    if (t == 0) atomicOr(&a.ctrl->err, kErrSlots);
+                    return;
+                }
+                if (remaining == 0) break;
+            }
+            for (int v = t; v < a.n; v += T) {
+                if (state[v] != ST_ROOT) continue;
+                int taken = 1;
+                for (int k = a.rowptr[v]; k < a.rowptr[v + 1]; k++) {
+                    const int u = a.col[k];
+                    if (u == v) continue;
+                    if (a.t > 0 && taken >= a.t) break;
+                    const uint8_t s = state[u];
+                    if (s == ST_CAND || s == ST_EXCL) {
+                        a.root_of[u] = v;
+                        a.pass_of[u] = pass;
+                        state[u] = ST_DONE;
+                        taken++;
+                    }
+                }
+                a.root_of[v] = v;
+                a.pass_of[v] = pass;
+                a.agg_size[v] = taken;
+                state[v] = ST_DONE;
+            }
+            __syncthreads();
+            int cnt = 0;
+            for (int v = t; v < a.n; v += T) {
+                const uint8_t s = state[v];
+                if (s == ST_EXCL) state[v] = ST_CAND;
+                cnt += (s == ST_EXCL || s == ST_CAND);
+            }
+            if (block_sum_big(cnt, red) == 0) {
+                pass++;
+                break;
+            }
+        }
+        pass++;
+        if (++rounds >= a.nslots) {
+            if (t == 0) atomicOr(&a.ctrl->err, kErrSlots);
+            return;
+        }
+    }
+    if (t == 0) a.ctrl->npasses = pass;
+}
+
 int launch_paa(Handle* h, int level, int n, const int* rowptr, const int* col,
                const uint64_t* prio, int t, int mode, const PaaBuffers& b, int* pass_of) {
     static int blocks_per_sm = 0;
@@ -333,6 +489,19 @@ int launch_paa(Handle* h, int level, int n, const int* rowptr, const int* col,
                 cudaSuccess ||
             blocks_per_sm < 1)
             blocks_per_sm = 1;
+    }
+    if (n <= kPaaSmallN) {  // one block, state in shared memory
+        static bool attr_set = false;
+        const size_t smem = (sizeof(uint64_t) + 2) * (size_t)kPaaSmallN;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_paa_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr_set = true;
+        }
+        PaaArgs a{n, rowptr, col, prio, b.state, b.b1, b.blocked, b.root_of, pass_of, b.agg_size,
+                  t, mode, b.slots, kMaxRoundSlots, h->ctrl};
+        k_paa_small<<<1, kPaaSmallThreads, smem, h->work>>>(a);
+        count_launch(h);
+        return check_cuda(cudaGetLastError());
     }
     int grid = blocks_per_sm * h->num_sms;
     int need = grid_for(n, kThreads);
@@ -607,12 +776,13 @@ int launch_compose(Handle* h, int n, int nc, const int* agg1, const int* aggptr1
 }
 
 // ---------------------------------------------------------------------------------------
-// l1-Jacobi data, Section 4.1: Minv_i = 1 / (a_ii + sum_{j!=i} |a_ij|), the row sum taken in
-// stored order; FP32 copies for the mixed-precision cycle.
+// Smoother data, Section 4.1: l1-Jacobi Minv_i = 1 / (a_ii + sum_{j!=i} |a_ij|) (row sum in
+// stored order), or damped Jacobi Minv_i = omega / a_ii; FP32 copies for the mixed cycle.
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads)
 k_minv(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
-       const double* __restrict__ val, double* __restrict__ minv64, float* __restrict__ minv32) {
+       const double* __restrict__ val, double omega, double* __restrict__ minv64,
+       float* __restrict__ minv32) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double diag = 0.0, off = 0.0;
@@ -620,7 +790,8 @@ k_minv(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
         if (col[k] == i) diag = val[k];
         else off = __dadd_rn(off, fabs(val[k]));
     }
-    double m = __ddiv_rn(1.0, __dadd_rn(diag, off));
+    // l1-Jacobi, or damped Jacobi omega / a_ii when omega > 0
+    double m = omega > 0.0 ? __ddiv_rn(omega, diag) : __ddiv_rn(1.0, __dadd_rn(diag, off));
     minv64[i] = m;
     if (minv32) minv32[i] = __double2float_rn(m);
 }
@@ -633,7 +804,8 @@ k_cast32(long long nnz, const double* __restrict__ v64, float* __restrict__ v32)
 
 int launch_level_finish(Handle* h, int n, long long nnz, const int* rowptr, const int* col,
                         const double* val64, double* minv64, float* minv32, float* val32) {
-    k_minv<<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, rowptr, col, val64, minv64, minv32);
+    k_minv<<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, rowptr, col, val64,
+                                                             h->p.jacobi_omega, minv64, minv32);
     count_launch(h);
     if (val32) {
         k_cast32<<<grid_for(nnz, kThreads), kThreads, 0, h->work>>>(nnz, val64, val32);

@@ -18,12 +18,6 @@ __device__ __forceinline__ T ld_stream(const T* p) {
     return __ldcs(p);
 }
 
-template <typename T, int MODE>
-__device__ __forceinline__ T rb_gather(const RBArgs<T>& a, int j) {
-    if constexpr (MODE == RB_PRE1) return mul_rn(a.minv[j], a.r[j]);
-    else if constexpr (MODE == RB_PROSMOOTH) return add_rn(a.x[j], a.e[a.agg[j]]);
-    else return a.x[j];
-}
 
 // Four consecutive matrix values with one 16-byte (FP32) or two 16-byte (FP64) loads.
 __device__ __forceinline__ void ld_val4(const float* p, float (&v)[4]) {
@@ -47,9 +41,11 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
     if (a.skip && *(volatile const int*)a.skip) return;
     __shared__ T sval[kChunk];
     __shared__ T sx[kChunk];
-    const int r0 = blockIdx.x * kRowsPerBlock;
-    const int r1 = min(a.n, r0 + kRowsPerBlock);
-    const int row = r0 + threadIdx.x;
+    const int lanes = kRowsPerBlock / a.rows;  // threads per row: 1, 2, 4 or 8
+    const int sub = threadIdx.x & (lanes - 1);
+    const int r0 = blockIdx.x * a.rows;
+    const int r1 = min(a.n, r0 + a.rows);
+    const int row = r0 + (int)threadIdx.x / lanes;
     const int k0 = a.rowptr[r0], k1 = a.rowptr[r1];
     const int ktot = a.rowptr[a.n];
     int rs = 0, re = 0;
@@ -91,13 +87,15 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
         }
         __syncthreads();
         const int lo = max(rs, c0), hi = min(re, c1);
-        for (int k = lo; k < hi; k++) acc = fma_rn(sval[k - c0], sx[k - c0], acc);
+        for (int k = lo + sub; k < hi; k += lanes) acc = fma_rn(sval[k - c0], sx[k - c0], acc);
         __syncthreads();
     }
+    // the lanes of a row combine their partial sums by a fixed shuffle tree
+    for (int o = lanes >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, lanes);
     double dv[ND > 0 ? ND : 1];
 #pragma unroll
     for (int k = 0; k < (ND > 0 ? ND : 1); k++) dv[k] = 0.0;
-    if (row < r1) {
+    if (row < r1 && sub == 0) {
         const int i = row;
         if constexpr (MODE == RB_PRE1) {
             a.y[i] = mul_rn(a.minv[i], a.r[i]);
@@ -124,7 +122,9 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
 
 template <typename T>
 int launch_rowblock(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
-    const int grid = grid_for(a.n, kRowsPerBlock);
+    if (h->p.tma_rows > 0 && a.n >= h->p.tma_rows)
+        return launch_rowblock_tma<T>(h, mode, ndots, a);  // matrix stream via bulk copies
+    const int grid = grid_for(a.n, a.rows);
     cudaStream_t st = h->work;
 #define RB_CASE(M, D)                                                 \
     if (mode == M && ndots == D) {                                    \

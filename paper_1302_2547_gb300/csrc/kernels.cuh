@@ -57,6 +57,7 @@ enum RBMode {
 template <typename T>
 struct RBArgs {
     int n;
+    int rows;  // rows per block: 256, 128, 64 or 32 (256 / rows threads share a row)
     const int* rowptr;
     const int* col;
     const T* val;
@@ -74,8 +75,18 @@ struct RBArgs {
     double* result;
     const int* skip;
 };
+// The vector entry a row-block kernel multiplies with column j in each mode.
+template <typename T, int MODE>
+__device__ __forceinline__ T rb_gather(const RBArgs<T>& a, int j) {
+    if constexpr (MODE == RB_PRE1) return mul_rn(a.minv[j], a.r[j]);
+    else if constexpr (MODE == RB_PROSMOOTH) return add_rn(a.x[j], a.e[a.agg[j]]);
+    else return a.x[j];
+}
+
 template <typename T>
 int launch_rowblock(Handle* h, int mode, int ndots, const RBArgs<T>& a);
+template <typename T>
+int launch_rowblock_tma(Handle* h, int mode, int ndots, const RBArgs<T>& a);
 
 template <typename T>
 int launch_restrict(Handle* h, int nc, const int* aggptr, const int* members, const T* s,

@@ -42,7 +42,8 @@ static cudaMemPool_t pool_for(int dev) {
 
 void* dalloc_bytes(Handle* h, size_t bytes, int* status, bool temp) {
     if (*status != UAAMG_OK) return nullptr;
-    bytes = (bytes + 255) & ~(size_t)255;
+    // at least 16 bytes of tail padding: bulk copies round their ranges up to 16 bytes
+    bytes = (bytes + 32 + 255) & ~(size_t)255;
     unsigned long long budget = g_budget.load();
     unsigned long long now = g_bytes.fetch_add(bytes) + bytes;
     if (budget && now > budget) {

@@ -123,12 +123,29 @@ void uaamg_server::worker_main(int wid) {
         bool need_setup = false;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
+            // the oldest request whose matrix is not being set up or solved by another
+            // worker (a handle serves one thread at a time; requests for a busy matrix keep
+            // queueing and are batched when it frees)
+            auto pick = [&]() {
+                for (auto it = queue.begin(); it != queue.end(); ++it) {
+                    bool busy = false;
+                    for (auto& e : cache)
+                        if (e.key == (*it)->A->key && e.users > 0) busy = true;
+                    if (!busy) return it;
+                }
+                return queue.end();
+            };
+            auto sel = queue.end();
+            cv_work.wait(lk, [&] {
+                if (stopping && queue.empty()) return true;
+                sel = pick();
+                return sel != queue.end();
+            });
             if (stopping && queue.empty()) break;
-            // continuous batching: the oldest request plus every queued request for the same
-            // matrix and tolerance, up to max_batch
-            auto first = queue.front();
-            queue.pop_front();
+            // continuous batching: that request plus every queued request for the same matrix
+            // and tolerance, up to max_batch
+            auto first = *sel;
+            queue.erase(sel);
             batch.push_back(first);
             for (auto it = queue.begin(); it != queue.end() && (int)batch.size() < max_batch;) {
                 if ((*it)->A->key == first->A->key && (*it)->tol == first->tol) {
@@ -152,6 +169,7 @@ void uaamg_server::worker_main(int wid) {
                     }
                     n_rejected += batch.size();
                     cv_done.notify_all();
+                    cv_work.notify_all();
                     continue;
                 }
                 if (!make_room(need)) {  // wait for memory: put the batch back at the front
@@ -216,6 +234,7 @@ void uaamg_server::worker_main(int wid) {
         n_done += R;
         n_batches++;
         cv_done.notify_all();
+        cv_work.notify_all();  // a matrix became free: queued requests for it can run
     }
     cudaStreamDestroy(stream);
 }

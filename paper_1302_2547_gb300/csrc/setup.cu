@@ -221,9 +221,15 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
         }
         h->nlev = l + 1;
     }
-    // l1-Jacobi data (Section 4.1) and FP32 copies on every level
+    // l1-Jacobi data (Section 4.1) and FP32 copies on every level; rows per block of the
+    // row-block kernels: as many as fit one shared-memory chunk at the level's mean row
+    // length, but few enough for at least four blocks per SM
     for (int l = 0; l < h->nlev; l++) {
         Level& L = h->lev[l];
+        const double avg = (double)L.nnz / (double)L.n;
+        int rb = kRowsPerBlock;
+        while (rb > 32 && (rb * avg > 0.9 * kChunk || (double)L.n / rb < 4.0 * h->num_sms)) rb >>= 1;
+        L.rb_rows = rb;
         L.minv64 = dalloc<double>(h, L.n, &st);
         if (mixed) {
             L.minv32 = dalloc<float>(h, L.n, &st);

@@ -46,11 +46,9 @@ static double class_bytes(const Handle* h, int cls) {
     const double n = L.n, z = (double)L.nnz;
     const double f = (h->p.precision == UAAMG_MIXED) ? 4.0 : 8.0;
     if (cls == UAAMG_KCLASS_SMOOTH0) {
-        // pre-smoother + residual: z(f+4) + 4(n+1) + r, Minv read + x, s written (4 n f);
-        // prolongation + post-smoother: z(f+4) + 4(n+1) + x, r, Minv, y (4 n f) + agg + e_c
-        const double pre = z * (f + 4) + 4 * (n + 1) + 4 * n * f;
-        const double post = z * (f + 4) + 4 * (n + 1) + 4 * n * f + 4 * n + (double)L.nc * f;
-        return 0.5 * (pre + post);
+        // first sweep + residual: matrix z(f+4), row pointers 4(n+1); r and Minv read, x and
+        // s written: 4 n f
+        return z * (f + 4) + 4 * (n + 1) + 4 * n * f;
     }
     if (cls == UAAMG_KCLASS_SPMV64) return z * 12.0 + 4 * (n + 1) + 3 * n * 8.0;
     return 0.0;
@@ -60,6 +58,7 @@ template <typename T>
 static RBArgs<T> rb_args(Handle* h, const Level& L) {
     RBArgs<T> a{};
     a.n = L.n;
+    a.rows = L.rb_rows;
     a.rowptr = L.rowptr;
     a.col = L.col;
     a.val = Prec<T>::val(L);
@@ -133,9 +132,7 @@ static int apply_B(Handle* h, int l, const T* in, T* out) {
         T* y = buf(k++);
         a.y = y;
         if (post >= 1) {
-            int ps = prof_begin(h, UAAMG_KCLASS_SMOOTH0, l);
             if ((st = launch_rowblock<T>(h, RB_PROSMOOTH, 0, a))) return st;
-            prof_end(h, ps);
         } else {
             if ((st = launch_prolong<T>(h, L.n, x, L.agg, ec, y, skip))) return st;
         }
@@ -213,6 +210,7 @@ static int outer_iteration(Handle* h) {
     {
         RBArgs<double> a{};
         a.n = n;
+        a.rows = L0.rb_rows;
         a.rowptr = L0.rowptr;
         a.col = L0.col;
         a.val = L0.val64;
@@ -302,6 +300,7 @@ static int true_residual(Handle* h) {
     Level& L0 = h->lev[0];
     RBArgs<double> a{};
     a.n = L0.n;
+    a.rows = L0.rb_rows;
     a.rowptr = L0.rowptr;
     a.col = L0.col;
     a.val = L0.val64;

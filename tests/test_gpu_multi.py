@@ -43,7 +43,7 @@ def test_solve_many_columns(oracle, name, make, kw, R, precision):
     h = U.uaamg_setup(A.rowptr, A.col, A.val, p)
     okeys = ("coarse_size", "max_levels", "max_agg_size", "pass_mode", "seed", "pre", "post",
              "kcycle_inner", "kcycle_tau", "max_iter", "agg_repeat", "kcycle_ratio",
-             "min_coarsening")
+             "min_coarsening", "jacobi_omega")
     H = oracle.Hierarchy(A.rowptr, A.col, A.val,
                          oracle.Params(**{k: getattr(p, k) for k in okeys}))
     try:

@@ -33,7 +33,7 @@ def _cuda():
 
 OR_KEYS = ("coarse_size", "max_levels", "max_agg_size", "pass_mode", "seed", "pre", "post",
            "kcycle_inner", "kcycle_tau", "max_iter", "agg_repeat", "kcycle_ratio",
-           "min_coarsening")
+           "min_coarsening", "jacobi_omega")
 
 
 def both(A, oracle, **kw):
@@ -85,6 +85,7 @@ SETUP_CASES = [
     ("random_real_twice", lambda: I.random_graph(2500, 9000, seed=2, integer_weights=False),
      {"max_agg_size": 3, "agg_repeat": 2}),
     ("grid2d_64_stop", lambda: I.grid2d(64), {"min_coarsening": 1e9}),
+    ("grid3d_21_damped", lambda: I.grid3d(21, sigma=0.25, seed=4), {"jacobi_omega": 0.6}),
 ]
 
 
@@ -155,6 +156,51 @@ def test_kcycle_operator(oracle, precision, fuse):
         U.uaamg_free(h)
 
 
+@pytest.mark.parametrize("precision", [U.UAAMG_FP64, U.UAAMG_MIXED])
+def test_tma_rowblock_path(oracle, precision):
+    """Every level forced onto the TMA-staged row-block kernels (tma_rows=1): ragged last row
+    blocks, fewer row blocks than persistent blocks, and a hub row longer than one stage
+    (2048 entries) that takes the direct path.  Two-level B (no inner products) against the
+    oracle at the FP64 operator bar, then full solves at the solve bars."""
+    n = 5001
+    hub = np.zeros(2600, dtype=np.int64)
+    rest = np.arange(1, n - 1)
+    ei = np.concatenate([hub, rest])
+    ej = np.concatenate([np.arange(1, 2601), rest + 1])
+    w = np.random.default_rng(11).uniform(0.5, 2.0, len(ei))
+    wD = np.zeros(n)
+    wD[n - 1] = 1.0
+    cases = [I.grid2d(40, 37), I.laplacian_from_edges(n, ei, ej, w, wD)]
+    tol_b = 1e-12 if precision == U.UAAMG_FP64 else 2e-5
+    for A in cases:
+        h, H, _ = both(A, oracle, precision=precision, max_levels=2, coarse_size=64,
+                       max_agg_size=0, agg_repeat=2, tma_rows=1)
+        try:
+            r = np.random.default_rng(4).standard_normal(A.n)
+            g, o = U.uaamg_apply_B(h, 0, r), H.apply_B(0, r)
+            assert np.linalg.norm(g - o) <= tol_b * np.linalg.norm(o)
+        finally:
+            U.uaamg_free(h)
+    for A in cases + [I.grid3d(30, sigma=0.25, seed=5)]:
+        tol = 1e-8
+        h, H, _ = both(A, oracle, precision=precision, tma_rows=1, max_agg_size=0)
+        try:
+            b = I.rhs_uniform(A.n, 2000)
+            x = np.zeros(A.n)
+            st, it, rr = U.uaamg_solve(h, b, x, tol)
+            xo, ito, rro, sto, _ = H.solve(b, tol)
+            assert st == 0 and sto == 0
+            Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+            bn = np.linalg.norm(b)
+            assert np.linalg.norm(b - Asp @ x) <= tol * bn * 1.0001
+            if precision == U.UAAMG_FP64:
+                assert abs(it - ito) <= 1, (it, ito)
+            else:
+                assert it <= ito + 5, (it, ito)
+        finally:
+            U.uaamg_free(h)
+
+
 SOLVE_CASES = [
     ("poisson2d_64", lambda: I.poisson2d_64(), {}),
     ("grid3d_32", lambda: I.grid3d(32, sigma=0.25, seed=1), {"max_agg_size": 0}),
@@ -165,6 +211,7 @@ SOLVE_CASES = [
     ("grid2d_90_pre2post2", lambda: I.grid2d(90, 70), {"pre": 2, "post": 2}),
     ("grid3d_36_bench_params", lambda: I.grid3d(36, sigma=0.25, seed=3), "BENCH"),
     ("rgg_30k_ratio", lambda: I.rgg(30000, 8.0, seed=2), {"max_agg_size": 0, "kcycle_ratio": 3.0}),
+    ("grid2d_100_damped", lambda: I.grid2d(100), {"jacobi_omega": 0.6}),
 ]
 
 

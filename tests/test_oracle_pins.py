@@ -549,3 +549,17 @@ def test_stagnation_stop(oracle, inputs):
     b = inputs.rhs_uniform(A.n, 1)
     x, it, rr, st, _ = stop.solve(b, 1e-10)
     assert st == 0 and np.linalg.norm(b - A.dense() @ x) <= 1e-10 * np.linalg.norm(b) * 1.0001
+
+
+def test_damped_jacobi_closed_form_and_solve(oracle, inputs):
+    """Damped Jacobi (Section 4.1): Minv_i = omega / a_ii, and the hierarchy still solves."""
+    A = inputs.grid2d(40, dirichlet=True)
+    H = oracle.Hierarchy(A.rowptr, A.col, A.val, oracle.Params(jacobi_omega=0.6))
+    assert np.all(H.minv(0) == 0.6 / 4.0)
+    rp, cc, vv = H.csr(1)
+    d = vv[np.concatenate([np.flatnonzero(cc[rp[i]:rp[i + 1]] == i) + rp[i]
+                           for i in range(H.n(1))])]
+    assert np.array_equal(H.minv(1), 0.6 / d)
+    b = inputs.rhs_uniform(A.n, 3)
+    x, it, rr, st, _ = H.solve(b, 1e-8)
+    assert st == 0 and np.linalg.norm(b - A.dense() @ x) <= 1e-8 * np.linalg.norm(b) * 1.0001
