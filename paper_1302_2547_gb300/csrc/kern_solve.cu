@@ -36,6 +36,8 @@ __device__ __forceinline__ void ld_val4(const double* p, double (&v)[4]) {
     v[3] = q1.y;
 }
 
+constexpr int kGrp = 2;  // four-entry groups a thread loads per batch
+
 template <typename T, int MODE, int ND>
 __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
     if (a.skip && *(volatile const int*)a.skip) return;
@@ -57,33 +59,49 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
     for (int c0 = k0; c0 < k1; c0 += kChunk) {
         const int c1 = min(k1, c0 + kChunk);
         // groups of four entries at 16-byte aligned indices; entries outside [c0, c1) are
-        // loaded (they lie inside the arrays) but not used
-#pragma unroll 2
-        for (int kb = (c0 & ~3) + 4 * (int)threadIdx.x; kb < c1; kb += 4 * kThreads) {
-            int j[4];
-            T v[4];
-            if (kb + 4 <= ktot) {
-                const int4 cj = __ldcs(reinterpret_cast<const int4*>(a.col + kb));
-                j[0] = cj.x;
-                j[1] = cj.y;
-                j[2] = cj.z;
-                j[3] = cj.w;
-                ld_val4(a.val + kb, v);
-            } else {
+        // loaded (they lie inside the arrays) but not used.  Each thread loads kGrp groups,
+        // then issues all their gathers before using any, so it waits for two memory round
+        // trips per batch instead of one per group.
+        for (int kb0 = (c0 & ~3) + 4 * (int)threadIdx.x; kb0 < c1; kb0 += 4 * kThreads * kGrp) {
+            int j[kGrp][4];
+            T v[kGrp][4];
+#pragma unroll
+            for (int g = 0; g < kGrp; g++) {
+                const int kb = kb0 + g * 4 * kThreads;
+                if (kb + 4 <= ktot && kb < c1) {
+                    const int4 cj = __ldcs(reinterpret_cast<const int4*>(a.col + kb));
+                    j[g][0] = cj.x;
+                    j[g][1] = cj.y;
+                    j[g][2] = cj.z;
+                    j[g][3] = cj.w;
+                    ld_val4(a.val + kb, v[g]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const bool in = kb < c1 && kb + e < ktot;
+                        j[g][e] = in ? a.col[kb + e] : 0;
+                        v[g][e] = in ? a.val[kb + e] : T(0);
+                    }
+                }
+            }
+            T xg[kGrp][4];
+#pragma unroll
+            for (int g = 0; g < kGrp; g++)
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    j[e] = (kb + e < ktot) ? a.col[kb + e] : 0;
-                    v[e] = (kb + e < ktot) ? a.val[kb + e] : T(0);
+                    const int k = kb0 + g * 4 * kThreads + e;
+                    xg[g][e] = (k >= c0 && k < c1) ? rb_gather<T, MODE>(a, j[g][e]) : T(0);
                 }
-            }
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const int k = kb + e;
-                if (k >= c0 && k < c1) {
-                    sval[k - c0] = v[e];
-                    sx[k - c0] = rb_gather<T, MODE>(a, j[e]);
+            for (int g = 0; g < kGrp; g++)
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int k = kb0 + g * 4 * kThreads + e;
+                    if (k >= c0 && k < c1) {
+                        sval[k - c0] = v[g][e];
+                        sx[k - c0] = xg[g][e];
+                    }
                 }
-            }
         }
         __syncthreads();
         const int lo = max(rs, c0), hi = min(re, c1);

@@ -5,14 +5,14 @@
 // a row block are one contiguous range of col/val; thread 0 copies the ranges of the next
 // two row blocks into a two-stage shared-memory ring with 1D bulk copies
 // (cp.async.bulk ... mbarrier::complete_tx), so the HBM stream of the matrix runs ahead
-// of the computation instead of sitting on each block's critical path.  The block then
-// gathers the vector entries of the staged columns, adds each row in stored order with
-// fused multiply-adds and applies the same fused epilogue as k_rowblock -- every vector
-// entry is bit-identical to that kernel's with one thread per row (the fused inner products
-// are summed in another fixed order, as each block now covers several row blocks).  A row
-// block whose entries do not
-// fit a stage is read directly from global memory.  Every wait on a stage barrier is bounded;
-// on timeout the block records kErrTimeout and leaves.
+// of the computation instead of sitting on each block's critical path.  Each thread then
+// walks its own row in the staged arrays, gathering the vector entries eight at a time,
+// adds the row in stored order with fused multiply-adds and applies the same fused epilogue
+// as k_rowblock: every vector entry is bit-identical to that kernel's with one thread per
+// row (the fused inner products are summed in another fixed order, as each block covers
+// several row blocks).  A row block whose entries do not fit a stage is read directly from
+// global memory.  Every wait on a stage barrier is bounded; on timeout the block records
+// kErrTimeout, waits (bounded) for its copies in flight and leaves.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -20,6 +20,7 @@ namespace uaamg {
 
 constexpr int kTmaRows = 256;
 constexpr int kTmaCap = 2048;              // entries per stage (16-byte aligned range)
+constexpr int kTmaBatch = 8;               // gathers a thread has in flight per row
 constexpr long long kTmaSpin = 1LL << 31;  // clock cycles before a stage wait gives up
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -57,16 +58,13 @@ template <typename T>
 struct TmaSmem {
     int col[2][kTmaCap];
     T val[2][kTmaCap];
-    T x[kTmaCap];
     uint64_t bar[2];
 };
 
-
-// Issues the copies of row block rb into stage s; returns false when it does not fit.
+// Issues the copies of the entry range [k0, k1) into stage s; false when it does not fit.
 template <typename T>
-__device__ __forceinline__ bool tma_issue(const RBArgs<T>& a, TmaSmem<T>& sm, int rb, int s) {
-    const int r0 = rb * kTmaRows, r1 = min(a.n, r0 + kTmaRows);
-    const int k0 = a.rowptr[r0], k1 = a.rowptr[r1];
+__device__ __forceinline__ bool tma_issue(const RBArgs<T>& a, TmaSmem<T>& sm, int k0, int k1,
+                                          int s) {
     const int a0 = k0 & ~3, a1 = (k1 + 3) & ~3;
     const int cnt = a1 - a0;
     if (cnt > kTmaCap || cnt <= 0) return false;
@@ -75,6 +73,27 @@ __device__ __forceinline__ bool tma_issue(const RBArgs<T>& a, TmaSmem<T>& sm, in
     bulk_g2s(sm.col[s], a.col + a0, (unsigned)cnt * 4u, &sm.bar[s]);
     bulk_g2s(sm.val[s], a.val + a0, (unsigned)cnt * (unsigned)sizeof(T), &sm.bar[s]);
     return true;
+}
+
+// One row's sum over entries [lo, hi) of col/val, in stored order; the vector entries of
+// kTmaBatch entries are gathered before the first is used.
+template <typename T, int MODE>
+__device__ __forceinline__ T row_sum(const RBArgs<T>& a, const int* col, const T* val, int lo,
+                                     int hi) {
+    T acc = T(0);
+    for (int k = lo; k < hi; k += kTmaBatch) {
+        T xg[kTmaBatch], vv[kTmaBatch];
+#pragma unroll
+        for (int u = 0; u < kTmaBatch; u++) {
+            const bool in = k + u < hi;
+            xg[u] = in ? rb_gather<T, MODE>(a, col[k + u]) : T(0);
+            vv[u] = in ? val[k + u] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kTmaBatch; u++)
+            if (k + u < hi) acc = fma_rn(vv[u], xg[u], acc);
+    }
+    return acc;
 }
 
 template <typename T, int MODE, int ND>
@@ -91,11 +110,14 @@ __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ct
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int s = 0; s < 2; s++) {
             const int rb = blockIdx.x + s * G;
-            staged[s] = (rb < nblk) ? (tma_issue<T>(a, sm, rb, s) ? 1 : 0) : 0;
+            staged[s] = 0;
+            if (rb < nblk)
+                staged[s] = tma_issue<T>(a, sm, a.rowptr[rb * kTmaRows],
+                                         a.rowptr[min(a.n, (rb + 1) * kTmaRows)], s) ? 1 : 0;
         }
     }
     __syncthreads();
-    unsigned phase[2] = {0u, 0u};
+    unsigned phase = 0u;  // bit s: parity of the next completion of stage s
     double dv[ND > 0 ? ND : 1];
 #pragma unroll
     for (int k = 0; k < (ND > 0 ? ND : 1); k++) dv[k] = 0.0;
@@ -106,7 +128,14 @@ __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ct
         const int s = it & 1;
         const int r0 = rb * kTmaRows, r1 = min(a.n, r0 + kTmaRows);
         const int row = r0 + threadIdx.x;
-        const int k0 = a.rowptr[r0], k1 = a.rowptr[r1];
+        // thread 0 loads the bounds of the row block it copies into this stage next, so the
+        // copy is issued without a memory round trip on the block's path
+        const int nrb = rb + 2 * G;
+        int nk0 = 0, nk1 = 0;
+        if (threadIdx.x == 0 && nrb < nblk) {
+            nk0 = a.rowptr[nrb * kTmaRows];
+            nk1 = a.rowptr[min(a.n, (nrb + 1) * kTmaRows)];
+        }
         int rs = 0, re = 0;
         T ri = T(0), mi = T(0), xi = T(0);
         int gi = 0;
@@ -124,8 +153,9 @@ __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ct
         }
         T acc = T(0);
         if (staged[s]) {
+            const int a0 = a.rowptr[r0] & ~3;
             long long t0 = clock64();
-            while (!mbar_try_wait(&sm.bar[s], phase[s])) {
+            while (!mbar_try_wait(&sm.bar[s], (phase >> s) & 1u)) {
                 if (clock64() - t0 > kTmaSpin) {
                     failed = true;
                     break;
@@ -139,28 +169,17 @@ __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ct
                     for (int q = 0; q < 2; q++) {
                         if (!staged[q]) continue;
                         const long long t1 = clock64();
-                        while (!mbar_try_wait(&sm.bar[q], phase[q]) && clock64() - t1 < kTmaSpin) {
+                        while (!mbar_try_wait(&sm.bar[q], (phase >> q) & 1u) &&
+                               clock64() - t1 < kTmaSpin) {
                         }
                     }
                 }
                 return;
             }
-            phase[s] ^= 1u;
-            const int a0 = k0 & ~3;
-            for (int k = k0 + threadIdx.x; k < k1; k += kThreads)
-                sm.x[k - k0] = rb_gather<T, MODE>(a, sm.col[s][k - a0]);
-            __syncthreads();
-            for (int k = rs; k < re; k++) acc = fma_rn(sm.val[s][k - a0], sm.x[k - k0], acc);
-        } else {  // entries beyond a stage: straight from global memory, in chunks
-            for (int c0 = k0; c0 < k1; c0 += kTmaCap) {
-                const int c1 = min(k1, c0 + kTmaCap);
-                for (int k = c0 + threadIdx.x; k < c1; k += kThreads)
-                    sm.x[k - c0] = rb_gather<T, MODE>(a, a.col[k]);
-                __syncthreads();
-                const int lo = max(rs, c0), hi = min(re, c1);
-                for (int k = lo; k < hi; k++) acc = fma_rn(a.val[k], sm.x[k - c0], acc);
-                __syncthreads();
-            }
+            phase ^= 1u << s;
+            if (row < r1) acc = row_sum<T, MODE>(a, sm.col[s], sm.val[s], rs - a0, re - a0);
+        } else if (row < r1) {  // entries beyond a stage: straight from global memory
+            acc = row_sum<T, MODE>(a, a.col, a.val, rs, re);
         }
         if (row < r1) {
             const int i = row;
@@ -184,12 +203,10 @@ __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ct
                 if constexpr (ND >= 3) dv[2] += xd * (double)a.d2[i];
             }
         }
-        __syncthreads();  // stage s and the gather buffer are free again
-        if (threadIdx.x == 0) {
-            const int nrb = rb + 2 * G;
-            staged[s] = (nrb < nblk) ? (tma_issue<T>(a, sm, nrb, s) ? 1 : 0) : 0;
-        }
+        // Stage s is free once every thread is past this barrier.  staged[s] is read next
+        // two iterations later, after at least one more barrier.
         __syncthreads();
+        if (threadIdx.x == 0) staged[s] = (nrb < nblk) ? (tma_issue<T>(a, sm, nk0, nk1, s) ? 1 : 0) : 0;
     }
     if constexpr (ND > 0) grid_reduce<ND>(dv, a.partials, a.counter, a.result);
 }

@@ -181,7 +181,11 @@ def test_tma_rowblock_path(oracle, precision):
             assert np.linalg.norm(g - o) <= tol_b * np.linalg.norm(o)
         finally:
             U.uaamg_free(h)
-    for A in cases + [I.grid3d(30, sigma=0.25, seed=5)]:
+    # The hub graph is rounding-sensitive even in the oracle alone (a relative 1e-15
+    # perturbation of b moves its count between 22 and 26 iterations), so only the residual
+    # bars and a loose count bar apply to it; the grids keep the +-1 FP64 bar.
+    solve_cases = [(cases[0], True), (cases[1], False), (I.grid3d(30, sigma=0.25, seed=5), True)]
+    for A, regular in solve_cases:
         tol = 1e-8
         h, H, _ = both(A, oracle, precision=precision, tma_rows=1, max_agg_size=0)
         try:
@@ -193,7 +197,10 @@ def test_tma_rowblock_path(oracle, precision):
             Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
             bn = np.linalg.norm(b)
             assert np.linalg.norm(b - Asp @ x) <= tol * bn * 1.0001
-            if precision == U.UAAMG_FP64:
+            assert np.linalg.norm(Asp @ (x - xo)) <= 2.0001 * tol * bn
+            if not regular:
+                assert it <= 1.5 * ito, (it, ito)
+            elif precision == U.UAAMG_FP64:
                 assert abs(it - ito) <= 1, (it, ito)
             else:
                 assert it <= ito + 5, (it, ito)
