@@ -43,7 +43,7 @@ extern "C" {
 #define UAAMG_OK 0
 #define UAAMG_ERR_INVALID_ARG 1   /* null pointer, out-of-range parameter */
 #define UAAMG_ERR_BAD_CSR 2       /* malformed, unsorted, asymmetric, non-finite, bad diag */
-#define UAAMG_ERR_NOT_SPD 3       /* Cholesky breakdown on the coarsest level */
+#define UAAMG_ERR_NOT_SPD 3       /* a pivot <= 0 while inverting the coarsest matrix */
 #define UAAMG_ERR_NO_CONVERGENCE 4 /* max_iter reached; iters/relres/x are still filled */
 #define UAAMG_ERR_OOM 5           /* device allocation failed */
 #define UAAMG_ERR_BUDGET 6        /* the library-wide device-memory budget would be exceeded */

@@ -36,8 +36,8 @@ struct Ctrl {
     int skip;                // level+1 of the K-cycle level skipping its second step, else 0
     int err;                 // kErr* bits
     unsigned int red_count;  // arrival counter of the last-block reductions
-    unsigned int bar_count;  // grid barrier arrivals
-    unsigned int bar_gen;    // grid barrier generation
+    unsigned int bar_count;  // grid barrier arrivals (zeroed before each cooperative launch)
+    unsigned int pad0;
     int npasses;             // written by the aggregation kernel
     int pad[2];
 };
@@ -179,29 +179,35 @@ __device__ __forceinline__ long long global_ns() {
     return t;
 }
 
-// Grid-wide barrier for a cooperatively launched kernel (all blocks co-resident).  The
-// wait is bounded: after kBarrierTimeoutNs the block records kErrTimeout and leaves; the
-// caller then stops.  Returns false once any block has timed out.
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The arrival counter only grows (the launcher
+// zeroes it): the k-th barrier is passed once it reaches (k+1) * gridDim.x, so an arrival
+// costs one atomic and no block has to reset or flip anything.  The wait polls with an
+// acquire load, first back to back, then with a short sleep, and gives up after
+// kBarrierTimeoutNs (kErrTimeout, returns false).
 __device__ __forceinline__ bool grid_barrier(Ctrl* c) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &c->bar_gen;
-        unsigned int g = *vgen;
         __threadfence();
-        unsigned int arrived = atomicAdd(&c->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
-        } else {
-            long long t0 = global_ns();
-            while (*vgen == g) {
-                if (global_ns() - t0 > kBarrierTimeoutNs) {
-                    atomicOr(&c->err, kErrTimeout);
-                    break;
-                }
-                __nanosleep(100);
+        const unsigned int arrived = atomicAdd(&c->bar_count, 1u);
+        const unsigned int target = (arrived / gridDim.x + 1u) * gridDim.x;
+        long long t0 = 0;
+        int spins = 0;
+        while ((int)(ld_acquire(&c->bar_count) - target) < 0) {
+            if (++spins < 64) continue;
+            const long long now = global_ns();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kBarrierTimeoutNs) {
+                atomicOr(&c->err, kErrTimeout);
+                break;
             }
+            __nanosleep(32);
         }
         __threadfence();
     }

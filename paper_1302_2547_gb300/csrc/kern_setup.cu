@@ -128,6 +128,8 @@ struct PaaArgs {
     uint8_t* state;
     uint64_t* b1;
     uint8_t* blocked;
+    int* list;        // two candidate lists of n entries (single-round mode)
+    uint64_t* cprio;  // n entries: priority while a candidate, else 0 (single-round mode)
     int* root_of;
     int* pass_of;
     int* agg_size;
@@ -159,6 +161,184 @@ __device__ __forceinline__ int block_sum_int(int v) {
     return r;
 }
 
+// Single-round passes (Algorithm 2 as printed) on candidate worklists, one cooperative
+// kernel per aggregation.  Pass p needs b1 of every vertex next to a candidate; two b1
+// buffers alternate between passes.
+//   pull pass (pass 0, and while the candidates are many): every vertex w computes
+//     b1[w] = max priority of the candidates in N[w] into the current buffer and clears
+//     the other one;
+//   push pass: each vertex w of the previous pass's list clears the old buffer at N[w]
+//     (exactly the entries that pass made nonzero) and, if still a candidate, raises the
+//     current buffer at N[w] to P_w with atomicMax.
+// Both build the list of this pass's candidates (warp-aggregated appends; its order does
+// not matter).  Then every listed candidate v becomes a root iff max_{u in N[v]} b1[u] = P_v
+// and takes its neighbours at once.  Fusing selection and aggregation is safe: a neighbour
+// w of a root v is never a root itself (P_v > P_w within distance 2) and no other root
+// reaches it (roots are >= 3 apart), so w has a single writer.
+// On small levels the sweeps are latency-bound chains (col -> state -> priority), so G
+// lanes share a vertex, one neighbour each, and the grid holds about one vertex per group:
+// a row of up to G entries costs one chain.  Large levels use G = 1.  Arrays written
+// inside the kernel are read through L2.
+constexpr int kPullDiv = 4;  // pull while more than n / kPullDiv candidates remain
+
+// Maximum over the G lanes of a vertex's group; every lane of the warp takes part.
+template <int G>
+__device__ __forceinline__ uint64_t group_max(uint64_t x) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, o, G);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
+constexpr int kPaaThreads = 1024;  // large blocks: fewer arrivals at each grid barrier
+
+constexpr int kPaaBatch = 4;  // neighbour steps whose loads are issued together
+
+template <int G>
+__global__ void __launch_bounds__(kPaaThreads, 2) k_paa_sr(PaaArgs a) {
+    const int n = a.n;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    // cp[v] = P_v while v is a candidate, 0 once aggregated: one load answers both "is it a
+    // candidate" and "with what priority"
+    unsigned long long* cp = reinterpret_cast<unsigned long long*>(a.cprio);
+    for (int v = tid; v < n; v += nthreads) {
+        cp[v] = a.prio[v];
+        a.root_of[v] = -1;
+        a.pass_of[v] = -1;
+    }
+    if (!grid_barrier(a.ctrl)) return;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (G - 1);  // lane within the vertex's group
+    const int gw = lane / G;         // group within the warp
+    const unsigned gmask = (unsigned)((1ull << G) - 1ull) << (gw * G);
+    const int wbase = (tid - lane) / G;  // this warp's first group
+    const int gstride = nthreads / G;
+    int prev_cnt = n, pass = 0;
+    while (true) {
+        uint64_t* bcur = a.b1 + (size_t)(pass & 1) * n;
+        uint64_t* bold = a.b1 + (size_t)((pass + 1) & 1) * n;
+        int* cur = a.list + (size_t)(pass & 1) * n;
+        const int* prev = a.list + (size_t)((pass + 1) & 1) * n;
+        const bool pull = pass == 0 || (long long)prev_cnt * kPullDiv > n;
+        const int span = pull ? n : prev_cnt;
+        for (int q0 = wbase; q0 < span; q0 += gstride) {  // uniform over the warp
+            const int q = q0 + gw;
+            const bool valid = q < span;
+            const int w = valid ? (pull ? q : __ldcg(prev + q)) : 0;
+            const int k0 = valid ? a.rowptr[w] : 0, k1 = valid ? a.rowptr[w + 1] : 0;
+            const unsigned long long pw = valid ? __ldcg(cp + w) : 0ull;
+            const bool cand = pw != 0ull;
+            const unsigned m = __ballot_sync(0xffffffffu, cand && sub == 0);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&a.slots[pass], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (cand && sub == 0) cur[base + __popc(m & ((1u << lane) - 1u))] = w;
+            const unsigned steps = __reduce_max_sync(0xffffffffu, (unsigned)(k1 - k0 + G - 1) / G);
+            uint64_t best = 0;
+            for (unsigned c0 = 0; c0 < steps; c0 += kPaaBatch) {
+                int u[kPaaBatch];
+#pragma unroll
+                for (int b = 0; b < kPaaBatch; b++) {
+                    const int k = k0 + (int)(c0 + b) * G + sub;
+                    u[b] = (c0 + b < steps && k < k1) ? a.col[k] : -1;
+                }
+                if (pull) {
+                    unsigned long long pu[kPaaBatch];
+#pragma unroll
+                    for (int b = 0; b < kPaaBatch; b++) pu[b] = u[b] >= 0 ? __ldcg(cp + u[b]) : 0ull;
+#pragma unroll
+                    for (int b = 0; b < kPaaBatch; b++) best = pu[b] > best ? pu[b] : best;
+                } else {
+#pragma unroll
+                    for (int b = 0; b < kPaaBatch; b++) {
+                        if (u[b] < 0) continue;
+                        bold[u[b]] = 0;
+                        if (cand) atomicMax(reinterpret_cast<unsigned long long*>(bcur + u[b]), pw);
+                    }
+                }
+            }
+            if (pull) {
+                best = group_max<G>(best);
+                if (valid && sub == 0) {
+                    bcur[w] = best;
+                    bold[w] = 0;
+                }
+            }
+        }
+        if (!grid_barrier(a.ctrl)) return;
+        const int cnt = *(volatile int*)&a.slots[pass];
+        if (cnt == 0) break;
+        for (int q0 = wbase; q0 < cnt; q0 += gstride) {
+            const int q = q0 + gw;
+            const bool valid = q < cnt;
+            const int v = valid ? __ldcg(cur + q) : 0;
+            const int k0 = valid ? a.rowptr[v] : 0, k1 = valid ? a.rowptr[v + 1] : 0;
+            const unsigned steps = __reduce_max_sync(0xffffffffu, (unsigned)(k1 - k0 + G - 1) / G);
+            uint64_t mx = 0;
+            for (unsigned c0 = 0; c0 < steps; c0 += kPaaBatch) {
+                int u[kPaaBatch];
+#pragma unroll
+                for (int b = 0; b < kPaaBatch; b++) {
+                    const int k = k0 + (int)(c0 + b) * G + sub;
+                    u[b] = (c0 + b < steps && k < k1) ? a.col[k] : -1;
+                }
+                unsigned long long bu[kPaaBatch];
+#pragma unroll
+                for (int b = 0; b < kPaaBatch; b++)
+                    bu[b] = u[b] >= 0 ? __ldcg(reinterpret_cast<const unsigned long long*>(bcur + u[b])) : 0ull;
+#pragma unroll
+                for (int b = 0; b < kPaaBatch; b++) mx = bu[b] > mx ? bu[b] : mx;
+            }
+            mx = group_max<G>(mx);
+            const bool root = valid && mx == a.prio[v];
+            if (!__any_sync(0xffffffffu, root)) continue;
+            // v's star aggregate: its unprocessed neighbours in ascending order, at most t-1;
+            // the group ranks each step's takers by lane, which keeps the stored order
+            int taken = 1;
+            for (unsigned c0 = 0; c0 < steps; c0 += kPaaBatch) {
+                int u[kPaaBatch];
+#pragma unroll
+                for (int b = 0; b < kPaaBatch; b++) {
+                    const int k = k0 + (int)(c0 + b) * G + sub;
+                    u[b] = (root && c0 + b < steps && k < k1) ? a.col[k] : -1;
+                }
+                bool take[kPaaBatch];
+#pragma unroll
+                for (int b = 0; b < kPaaBatch; b++)
+                    take[b] = u[b] >= 0 && u[b] != v && __ldcg(cp + u[b]) != 0ull;
+#pragma unroll
+                for (int b = 0; b < kPaaBatch; b++) {
+                    const unsigned bm = __ballot_sync(0xffffffffu, take[b]) & gmask;
+                    const int room = a.t > 0 ? a.t - taken : 0x7fffffff;
+                    if (take[b] && __popc(bm & ((1u << lane) - 1u)) < room) {
+                        a.root_of[u[b]] = v;
+                        a.pass_of[u[b]] = pass;
+                        cp[u[b]] = 0ull;
+                    }
+                    taken += min(__popc(bm), room);
+                }
+            }
+            if (root && sub == 0) {
+                a.root_of[v] = v;
+                a.pass_of[v] = pass;
+                a.agg_size[v] = taken;
+                cp[v] = 0ull;
+            }
+        }
+        if (!grid_barrier(a.ctrl)) return;
+        prev_cnt = cnt;
+        if (++pass >= a.nslots) {
+            if (tid == 0) atomicOr(&a.ctrl->err, kErrSlots);
+            return;
+        }
+    }
+    if (tid == 0) a.ctrl->npasses = pass;
+}
+
+// Maximal mode: every vertex per sweep, rounds of coarse-vertex selection then aggregation.
 __global__ void __launch_bounds__(kThreads) k_paa(PaaArgs a) {
     const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
     const int gs = gridDim.x * blockDim.x;
@@ -169,70 +349,6 @@ __global__ void __launch_bounds__(kThreads) k_paa(PaaArgs a) {
     }
     if (!grid_barrier(a.ctrl)) return;
     int slot = 0, pass = 0;
-    if (a.mode == UAAMG_PASS_SINGLE_ROUND) {
-        // One round per pass (Algorithm 2 as printed), two sweeps and two grid barriers per
-        // pass: (1) b1 and the count of unprocessed vertices; (2) every local maximum becomes
-        // a root and takes its neighbours at once.  Fusing selection and aggregation is safe:
-        // a neighbour w of a root v is never a root itself (P_v > P_w within distance 2) and
-        // no other root reaches it (roots are >= 3 apart), so w has a single writer, and w's
-        // own thread selects nothing whether it reads w's old or new state.
-        while (true) {
-            int cnt = 0;
-            for (int v = g0; v < a.n; v += gs) {
-                const int k0 = a.rowptr[v], k1 = a.rowptr[v + 1];
-                uint64_t best = 0;
-                for (int k = k0; k < k1; k++) {
-                    const int u = a.col[k];
-                    if (ld_state(a.state + u) == ST_CAND) {
-                        const uint64_t pu = a.prio[u];
-                        best = pu > best ? pu : best;
-                    }
-                }
-                a.b1[v] = best;
-                cnt += (ld_state(a.state + v) == ST_CAND);
-            }
-            cnt = block_sum_int(cnt);
-            if (threadIdx.x == 0 && cnt) atomicAdd(&a.slots[slot], cnt);
-            if (!grid_barrier(a.ctrl)) return;
-            const int remaining = *(volatile int*)&a.slots[slot];
-            slot++;
-            if (remaining == 0) break;
-            if (slot >= a.nslots) {
-                if (g0 == 0) atomicOr(&a.ctrl->err, kErrSlots);
-                return;
-            }
-            for (int v = g0; v < a.n; v += gs) {
-                if (ld_state(a.state + v) != ST_CAND) continue;
-                const int k0 = a.rowptr[v], k1 = a.rowptr[v + 1];
-                uint64_t m = 0;
-                for (int k = k0; k < k1; k++) {
-                    const uint64_t bu = __ldcg(reinterpret_cast<const unsigned long long*>(a.b1 + a.col[k]));
-                    m = bu > m ? bu : m;
-                }
-                if (m != a.prio[v]) continue;
-                int taken = 1;  // v is a root: its star aggregate
-                for (int k = k0; k < k1; k++) {
-                    const int u = a.col[k];
-                    if (u == v) continue;
-                    if (a.t > 0 && taken >= a.t) break;
-                    if (ld_state(a.state + u) == ST_CAND) {
-                        a.root_of[u] = v;
-                        a.pass_of[u] = pass;
-                        a.state[u] = ST_DONE;
-                        taken++;
-                    }
-                }
-                a.root_of[v] = v;
-                a.pass_of[v] = pass;
-                a.agg_size[v] = taken;
-                a.state[v] = ST_DONE;
-            }
-            if (!grid_barrier(a.ctrl)) return;
-            pass++;
-        }
-        if (g0 == 0) a.ctrl->npasses = pass;
-        return;
-    }
     while (true) {
         // (A) coarse vertices of this pass
         while (true) {
@@ -356,121 +472,75 @@ __global__ void __launch_bounds__(kPaaSmallThreads, 1) k_paa_small(PaaArgs a) {
     __syncthreads();
     int pass = 0, rounds = 0;
     while (true) {
-        if (a.mode == UAAMG_PASS_SINGLE_ROUND) {
-            // sweep 1: b1 and the count of unprocessed vertices
-            int cnt = 0;
+        // maximal set per pass: rounds until no candidate remains, then aggregation
+        while (true) {
             for (int v = t; v < a.n; v += T) {
                 uint64_t best = 0;
+                int blk = 0;
                 for (int k = a.rowptr[v]; k < a.rowptr[v + 1]; k++) {
                     const int u = a.col[k];
-                    if (state[u] == ST_CAND) {
+                    const uint8_t s = state[u];
+                    blk |= (s == ST_ROOT);
+                    if (s == ST_CAND) {
                         const uint64_t pu = a.prio[u];
                         best = pu > best ? pu : best;
                     }
                 }
                 b1[v] = best;
-                cnt += (state[v] == ST_CAND);
-            }
-            if (block_sum_big(cnt, red) == 0) break;
-            // sweep 2: local maxima become roots and take their neighbours (see k_paa)
-            for (int v = t; v < a.n; v += T) {
-                if (state[v] != ST_CAND) continue;
-                const int k0 = a.rowptr[v], k1 = a.rowptr[v + 1];
-                uint64_t m = 0;
-                for (int k = k0; k < k1; k++) {
-                    const uint64_t bu = b1[a.col[k]];
-                    m = bu > m ? bu : m;
-                }
-                if (m != a.prio[v]) continue;
-                int taken = 1;
-                for (int k = k0; k < k1; k++) {
-                    const int u = a.col[k];
-                    if (u == v) continue;
-                    if (a.t > 0 && taken >= a.t) break;
-                    if (state[u] == ST_CAND) {
-                        a.root_of[u] = v;
-                        a.pass_of[u] = pass;
-                        state[u] = ST_DONE;
-                        taken++;
-                    }
-                }
-                a.root_of[v] = v;
-                a.pass_of[v] = pass;
-                a.agg_size[v] = taken;
-                state[v] = ST_DONE;
-            }
-            __syncthreads();
-        } else {
-            // maximal set per pass: rounds until no candidate remains, then aggregation
-            while (true) {
-                for (int v = t; v < a.n; v += T) {
-                    uint64_t best = 0;
-                    int blk = 0;
-                    for (int k = a.rowptr[v]; k < a.rowptr[v + 1]; k++) {
-                        const int u = a.col[k];
-                        const uint8_t s = state[u];
-                        blk |= (s == ST_ROOT);
-                        if (s == ST_CAND) {
-                            const uint64_t pu = a.prio[u];
-                            best = pu > best ? pu : best;
-                        }
-                    }
-                    b1[v] = best;
-                    blocked[v] = (uint8_t)blk;
-                }
-                __syncthreads();
-                int cnt = 0;
-                for (int v = t; v < a.n; v += T) {
-                    if (state[v] != ST_CAND) continue;
-                    uint64_t m = 0;
-                    int blk = 0;
-                    for (int k = a.rowptr[v]; k < a.rowptr[v + 1]; k++) {
-                        const int u = a.col[k];
-                        blk |= blocked[u];
-                        m = b1[u] > m ? b1[u] : m;
-                    }
-                    if (blk) state[v] = ST_EXCL;
-                    else if (m == a.prio[v]) state[v] = ST_ROOT;
-                    else cnt++;
-                }
-                const int remaining = block_sum_big(cnt, red);
-                if (++rounds >= a.nslots) {
-                    if (t == 0) atomicOr(&a.ctrl->err, kErrSlots);
-                    return;
-                }
-                if (remaining == 0) break;
-            }
-            for (int v = t; v < a.n; v += T) {
-                if (state[v] != ST_ROOT) continue;
-                int taken = 1;
-                for (int k = a.rowptr[v]; k < a.rowptr[v + 1]; k++) {
-                    const int u = a.col[k];
-                    if (u == v) continue;
-                    if (a.t > 0 && taken >= a.t) break;
-                    const uint8_t s = state[u];
-                    if (s == ST_CAND || s == ST_EXCL) {
-                        a.root_of[u] = v;
-                        a.pass_of[u] = pass;
-                        state[u] = ST_DONE;
-                        taken++;
-                    }
-                }
-                a.root_of[v] = v;
-                a.pass_of[v] = pass;
-                a.agg_size[v] = taken;
-                state[v] = ST_DONE;
+                blocked[v] = (uint8_t)blk;
             }
             __syncthreads();
             int cnt = 0;
             for (int v = t; v < a.n; v += T) {
-                const uint8_t s = state[v];
-                if (s == ST_EXCL) state[v] = ST_CAND;
-                cnt += (s == ST_EXCL || s == ST_CAND);
+                if (state[v] != ST_CAND) continue;
+                uint64_t m = 0;
+                int blk = 0;
+                for (int k = a.rowptr[v]; k < a.rowptr[v + 1]; k++) {
+                    const int u = a.col[k];
+                    blk |= blocked[u];
+                    m = b1[u] > m ? b1[u] : m;
+                }
+                if (blk) state[v] = ST_EXCL;
+                else if (m == a.prio[v]) state[v] = ST_ROOT;
+                else cnt++;
             }
-            if (block_sum_big(cnt, red) == 0) {
-                pass++;
-                break;
+            const int remaining = block_sum_big(cnt, red);
+            if (++rounds >= a.nslots) {
+                if (t == 0) atomicOr(&a.ctrl->err, kErrSlots);
+                return;
             }
+            if (remaining == 0) break;
+        }
+        for (int v = t; v < a.n; v += T) {
+            if (state[v] != ST_ROOT) continue;
+            int taken = 1;
+            for (int k = a.rowptr[v]; k < a.rowptr[v + 1]; k++) {
+                const int u = a.col[k];
+                if (u == v) continue;
+                if (a.t > 0 && taken >= a.t) break;
+                const uint8_t s = state[u];
+                if (s == ST_CAND || s == ST_EXCL) {
+                    a.root_of[u] = v;
+                    a.pass_of[u] = pass;
+                    state[u] = ST_DONE;
+                    taken++;
+                }
+            }
+            a.root_of[v] = v;
+            a.pass_of[v] = pass;
+            a.agg_size[v] = taken;
+            state[v] = ST_DONE;
+        }
+        __syncthreads();
+        int cnt = 0;
+        for (int v = t; v < a.n; v += T) {
+            const uint8_t s = state[v];
+            if (s == ST_EXCL) state[v] = ST_CAND;
+            cnt += (s == ST_EXCL || s == ST_CAND);
+        }
+        if (block_sum_big(cnt, red) == 0) {
+            pass++;
+            break;
         }
         pass++;
         if (++rounds >= a.nslots) {
@@ -481,51 +551,80 @@ __global__ void __launch_bounds__(kPaaSmallThreads, 1) k_paa_small(PaaArgs a) {
     if (t == 0) a.ctrl->npasses = pass;
 }
 
-int launch_paa(Handle* h, int level, int n, const int* rowptr, const int* col,
-               const uint64_t* prio, int t, int mode, const PaaBuffers& b, int* pass_of) {
+constexpr int kPaaLanesMaxN = 32768;  // largest level that shares lanes over a row
+
+template <int G>
+static int launch_paa_sr(Handle* h, const PaaArgs& a, int* grid) {
     static int blocks_per_sm = 0;
     if (!blocks_per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_paa, kThreads, 0) !=
-                cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_paa_sr<G>,
+                                                          kPaaThreads, 0) != cudaSuccess ||
             blocks_per_sm < 1)
             blocks_per_sm = 1;
     }
-    if (n <= kPaaSmallN) {  // one block, state in shared memory
+    *grid = blocks_per_sm * h->num_sms;
+    const int need = grid_for((long long)a.n * G, kPaaThreads);
+    if (*grid > need) *grid = need;
+    void* args[] = {const_cast<PaaArgs*>(&a)};
+    return check_cuda(cudaLaunchCooperativeKernel((const void*)k_paa_sr<G>, dim3(*grid),
+                                                  dim3(kPaaThreads), args, 0, h->work));
+}
+
+int launch_paa(Handle* h, int level, int n, long long nnz, const int* rowptr, const int* col,
+               const uint64_t* prio, int t, int mode, const PaaBuffers& b, int* pass_of) {
+    PaaArgs a{n, rowptr, col, prio, b.state, b.b1, b.blocked, b.list, b.cprio, b.root_of,
+              pass_of, b.agg_size, t, mode, b.slots, kMaxRoundSlots, h->ctrl};
+    cudaMemsetAsync(b.slots, 0, sizeof(int) * kMaxRoundSlots, h->work);
+    if (mode == UAAMG_PASS_MAXIMAL && n <= kPaaSmallN) {  // one block, state in shared memory
         static bool attr_set = false;
         const size_t smem = (sizeof(uint64_t) + 2) * (size_t)kPaaSmallN;
         if (!attr_set) {
             cudaFuncSetAttribute(k_paa_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr_set = true;
         }
-        PaaArgs a{n, rowptr, col, prio, b.state, b.b1, b.blocked, b.root_of, pass_of, b.agg_size,
-                  t, mode, b.slots, kMaxRoundSlots, h->ctrl};
         k_paa_small<<<1, kPaaSmallThreads, smem, h->work>>>(a);
         count_launch(h);
         return check_cuda(cudaGetLastError());
     }
-    int grid = blocks_per_sm * h->num_sms;
-    int need = grid_for(n, kThreads);
-    if (grid > need) grid = need;
-    cudaMemsetAsync(b.slots, 0, sizeof(int) * kMaxRoundSlots, h->work);
-    cudaMemsetAsync(&h->ctrl->bar_count, 0, 2 * sizeof(unsigned int), h->work);
-    PaaArgs a{n, rowptr, col, prio, b.state, b.b1, b.blocked, b.root_of, pass_of, b.agg_size,
-              t, mode, b.slots, kMaxRoundSlots, h->ctrl};
-    void* args[] = {&a};
+    cudaMemsetAsync(&h->ctrl->bar_count, 0, sizeof(unsigned int), h->work);
     ProfSlot ps{};
-    bool prof = (h->prof_class == UAAMG_KCLASS_PAA && level == 0);
+    const bool prof = (h->prof_class == UAAMG_KCLASS_PAA && level == 0);
     if (prof) {
         cudaEventCreate(&ps.a);
         cudaEventCreate(&ps.b);
         cudaEventRecord(ps.a, h->work);
     }
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_paa, dim3(grid), dim3(kThreads),
-                                                args, 0, h->work);
+    int st = UAAMG_OK;
+    if (mode == UAAMG_PASS_SINGLE_ROUND) {
+        // Large levels are throughput-bound: one lane per vertex.  Small ones are bound by
+        // the latency of each sweep's load chain: lanes per vertex from the row length.
+        const long long avg = n > 0 ? (nnz + n - 1) / n : 1;
+        int grid = 0;
+        if (n > kPaaLanesMaxN) st = launch_paa_sr<1>(h, a, &grid);
+        else if (avg <= 8) st = launch_paa_sr<8>(h, a, &grid);
+        else if (avg <= 16) st = launch_paa_sr<16>(h, a, &grid);
+        else st = launch_paa_sr<32>(h, a, &grid);
+    } else {
+        static int blocks_per_sm = 0;
+        if (!blocks_per_sm) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_paa, kThreads, 0) !=
+                    cudaSuccess ||
+                blocks_per_sm < 1)
+                blocks_per_sm = 1;
+        }
+        int grid = blocks_per_sm * h->num_sms;
+        const int need = grid_for(n, kThreads);
+        if (grid > need) grid = need;
+        void* args[] = {&a};
+        st = check_cuda(cudaLaunchCooperativeKernel((const void*)k_paa, dim3(grid),
+                                                    dim3(kThreads), args, 0, h->work));
+    }
     if (prof) {
         cudaEventRecord(ps.b, h->work);
         h->prof_slots.push_back(ps);
     }
     count_launch(h);
-    return check_cuda(e);
+    return st;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -827,73 +926,70 @@ k_dense_gather(int n, const int* __restrict__ rowptr, const int* __restrict__ co
     for (int k = rowptr[i]; k < rowptr[i + 1]; k++) D[(size_t)i * n + col[k]] = val[k];
 }
 
-// Left-looking Cholesky in one block: for column j, warp w computes the dot products of
-// rows i = j + w, j + w + 32, ... with row j over k < j (lanes over k), first the diagonal.
-__global__ void __launch_bounds__(1024)
-k_chol_factor(int n, double* __restrict__ D, Ctrl* ctrl) {
-    __shared__ int bad;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
+// Inverse of the SPD coarsest matrix by Gauss-Jordan elimination without pivoting: the
+// pivots are the leading diagonal entries of successive Schur complements, positive for an
+// SPD matrix, and a pivot <= 0 reports kErrNotSpd.  Step j maps the current iterate (one
+// buffer) to the next (the other) entry by entry,
+//   new_jj = 1/p,  new_jk = a_jk/p,  new_ij = -a_ij/p,  new_ik = a_ik - a_ij (a_jk/p),
+// with p = a_jj, so the whole grid works on one step and one grid barrier separates steps.
+// Buffers written by other blocks are read through L2 only (__ldcg).
+__global__ void __launch_bounds__(kThreads)
+k_gj_inverse(int n, double* __restrict__ A, double* __restrict__ B, Ctrl* ctrl) {
+    const int nn = n * n;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    double* src = A;
+    double* dst = B;
     for (int j = 0; j < n; j++) {
-        if (warp == 0) {
-            double s = 0.0;
-            for (int k = lane; k < j; k += 32) s += D[(size_t)j * n + k] * D[(size_t)j * n + k];
-            s = warp_sum(s);
-            if (lane == 0) {
-                const double d = D[(size_t)j * n + j] - s;
-                if (!(d > 0.0)) bad = 1;
-                else D[(size_t)j * n + j] = sqrt(d);
-            }
-        }
-        __syncthreads();
-        if (bad) {
-            if (threadIdx.x == 0) atomicOr(&ctrl->err, kErrNotSpd);
+        const double p = __ldcg(&src[(size_t)j * n + j]);
+        if (!(p > 0.0)) {  // every thread sees the same pivot, so all leave together
+            if (tid == 0) atomicOr(&ctrl->err, kErrNotSpd);
             return;
         }
-        const double ljj = D[(size_t)j * n + j];
-        for (int i = j + 1 + warp; i < n; i += nw) {
-            double s = 0.0;
-            for (int k = lane; k < j; k += 32) s += D[(size_t)i * n + k] * D[(size_t)j * n + k];
-            s = warp_sum(s);
-            if (lane == 0) D[(size_t)i * n + j] = (D[(size_t)i * n + j] - s) / ljj;
+        const double q = 1.0 / p;
+        for (int e = tid; e < nn; e += stride) {
+            const int i = e / n, k = e - i * n;
+            double v;
+            if (i == j) {
+                v = (k == j) ? q : __ldcg(&src[(size_t)j * n + k]) * q;
+            } else if (k == j) {
+                v = -__ldcg(&src[(size_t)i * n + j]) * q;
+            } else {
+                const double ajk = __ldcg(&src[(size_t)j * n + k]) * q;
+                v = fma(-__ldcg(&src[(size_t)i * n + j]), ajk, __ldcg(&src[e]));
+            }
+            dst[e] = v;
         }
-        __syncthreads();
+        if (!grid_barrier(ctrl)) return;
+        double* t = src;
+        src = dst;
+        dst = t;
     }
-}
-
-// Column c of the inverse, one warp per column: L y = e_c forward, then L^T x = y backward,
-// each step a warp-parallel dot product; y lives in shared memory.
-__global__ void __launch_bounds__(32)
-k_chol_inverse_cols(int n, const double* __restrict__ L, double* __restrict__ X) {
-    __shared__ double y[kMaxCoarsest];
-    const int c = blockIdx.x, lane = threadIdx.x;
-    for (int i = lane; i < n; i += 32) y[i] = 0.0;
-    __syncwarp();
-    for (int i = c; i < n; i++) {
-        double s = 0.0;
-        for (int k = c + lane; k < i; k += 32) s += L[(size_t)i * n + k] * y[k];
-        s = warp_sum(s);
-        if (lane == 0) y[i] = ((i == c ? 1.0 : 0.0) - s) / L[(size_t)i * n + i];
-        __syncwarp();
-    }
-    for (int i = n - 1; i >= 0; i--) {
-        double s = 0.0;
-        for (int k = i + 1 + lane; k < n; k += 32) s += L[(size_t)k * n + i] * y[k];
-        s = warp_sum(s);
-        if (lane == 0) y[i] = (y[i] - s) / L[(size_t)i * n + i];
-        __syncwarp();
-    }
-    for (int i = lane; i < n; i += 32) X[(size_t)i * n + c] = y[i];
+    if (src != B)  // n even: the inverse ended in A
+        for (int e = tid; e < nn; e += stride) B[e] = __ldcg(&src[e]);
 }
 
 int launch_dense_coarsest(Handle* h, int n, const int* rowptr, const int* col,
                           const double* val, double* work, double* inv) {
+    static int blocks_per_sm = 0;
+    if (!blocks_per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_gj_inverse, kThreads,
+                                                          0) != cudaSuccess ||
+            blocks_per_sm < 1)
+            blocks_per_sm = 1;
+    }
     cudaMemsetAsync(work, 0, sizeof(double) * (size_t)n * n, h->work);
     k_dense_gather<<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, rowptr, col, val, work);
-    k_chol_factor<<<1, 1024, 0, h->work>>>(n, work, h->ctrl);
-    k_chol_inverse_cols<<<n, 32, 0, h->work>>>(n, work, inv);
-    count_launch(h, 3);
+    int grid = blocks_per_sm * h->num_sms;
+    const int need = grid_for((long long)n * n, kThreads);
+    if (grid > need) grid = need;
+    cudaMemsetAsync(&h->ctrl->bar_count, 0, sizeof(unsigned int), h->work);
+    Ctrl* ctrl = h->ctrl;
+    void* args[] = {&n, &work, &inv, &ctrl};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_gj_inverse, dim3(grid),
+                                                dim3(kThreads), args, 0, h->work);
+    count_launch(h, 2);
+    if (e != cudaSuccess) return check_cuda(e);
     return check_cuda(cudaGetLastError());
 }
 

@@ -16,13 +16,15 @@ int launch_priority(Handle* h, int n, const int* rowptr, const int* col, uint32_
                     uint64_t* prio);
 struct PaaBuffers {
     uint8_t* state;
-    uint64_t* b1;
+    uint64_t* b1;  // 2 n entries
     uint8_t* blocked;
+    int* list;     // 2 n entries
+    uint64_t* cprio;  // n entries
     int* root_of;
     int* agg_size;
     int* slots;
 };
-int launch_paa(Handle* h, int level, int n, const int* rowptr, const int* col,
+int launch_paa(Handle* h, int level, int n, long long nnz, const int* rowptr, const int* col,
                const uint64_t* prio, int t, int mode, const PaaBuffers& b, int* pass_of);
 int launch_root_flags(Handle* h, int n, const int* root_of, const int* agg_size, int* f, int* g);
 int launch_renumber(Handle* h, int n, const int* root_of, const int* cid, const int* start,

@@ -6,7 +6,7 @@
 // cudaMalloc / cudaFree because those calls synchronise the device or are forbidden while
 // other work is in flight.  This entry point takes only the caller's input and output
 // buffers.  Its scratch lives in the file-scope device array below, which every GPU that
-// loads the library holds until the process exits (kStaticBytes, about 12 MB), so the
+// loads the library holds until the process exits (kStaticBytes, about 19 MB), so the
 // graph may have at most kStaticMaxN vertices.
 #include <mutex>
 
@@ -24,9 +24,11 @@ constexpr size_t kOffTot = a256(kOffCtrl + sizeof(Ctrl));
 constexpr size_t kOffSlots = a256(kOffTot + 4 * sizeof(int));
 constexpr size_t kOffPrio = a256(kOffSlots + sizeof(int) * (size_t)kMaxRoundSlots);
 constexpr size_t kOffB1 = a256(kOffPrio + sizeof(uint64_t) * kStaticMaxN);
-constexpr size_t kOffState = a256(kOffB1 + sizeof(uint64_t) * kStaticMaxN);
+constexpr size_t kOffState = a256(kOffB1 + 2 * sizeof(uint64_t) * kStaticMaxN);
 constexpr size_t kOffBlocked = a256(kOffState + kStaticMaxN);
-constexpr size_t kOffRootOf = a256(kOffBlocked + kStaticMaxN);
+constexpr size_t kOffList = a256(kOffBlocked + kStaticMaxN);
+constexpr size_t kOffCprio = a256(kOffList + 2 * sizeof(int) * kStaticMaxN);
+constexpr size_t kOffRootOf = a256(kOffCprio + sizeof(uint64_t) * kStaticMaxN);
 constexpr size_t kOffAggSize = a256(kOffRootOf + sizeof(int) * kStaticMaxN);
 constexpr size_t kOffPassOf = a256(kOffAggSize + sizeof(int) * kStaticMaxN);
 constexpr size_t kOffF = a256(kOffPassOf + sizeof(int) * kStaticMaxN);
@@ -89,6 +91,8 @@ extern "C" int uaamg_aggregate_static(const uaamg_csr* A, int32_t max_agg_size,
     pb.state = s + kOffState;
     pb.b1 = reinterpret_cast<uint64_t*>(s + kOffB1);
     pb.blocked = s + kOffBlocked;
+    pb.list = reinterpret_cast<int*>(s + kOffList);
+    pb.cprio = reinterpret_cast<uint64_t*>(s + kOffCprio);
     pb.root_of = reinterpret_cast<int*>(s + kOffRootOf);
     pb.agg_size = reinterpret_cast<int*>(s + kOffAggSize);
     pb.slots = reinterpret_cast<int*>(s + kOffSlots);
@@ -111,7 +115,8 @@ extern "C" int uaamg_aggregate_static(const uaamg_csr* A, int32_t max_agg_size,
     if ((st = check_cuda(cudaStreamSynchronize(h.work)))) return st;
     if (hc.err) return UAAMG_ERR_BAD_CSR;
     if ((st = launch_priority(&h, n, A->rowptr, A->col, static_level_salt(seed), prio))) return st;
-    if ((st = launch_paa(&h, 0, n, A->rowptr, A->col, prio, max_agg_size, pass_mode, pb, pass_of)))
+    if ((st = launch_paa(&h, 0, n, A->nnz, A->rowptr, A->col, prio, max_agg_size, pass_mode, pb,
+                          pass_of)))
         return st;
     if ((st = launch_root_flags(&h, n, pb.root_of, pb.agg_size, f, g))) return st;
     if ((st = scan_exclusive(&h, f, f, n, d_tot, scan_tmp))) return st;

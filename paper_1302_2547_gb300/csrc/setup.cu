@@ -56,7 +56,7 @@ static int aggregate_stage(Handle* h, int prof_level, const Csr& G, uint32_t sal
                            uint64_t* prio, int* pass_of, HostReadback* hb, Agg* out) {
     int st;
     if ((st = launch_priority(h, G.n, G.rowptr, G.col, salt, prio))) return st;
-    if ((st = launch_paa(h, prof_level, G.n, G.rowptr, G.col, prio, h->p.max_agg_size,
+    if ((st = launch_paa(h, prof_level, G.n, G.nnz, G.rowptr, G.col, prio, h->p.max_agg_size,
                          h->p.pass_mode, S.pb, pass_of)))
         return st;
     if ((st = launch_root_flags(h, G.n, S.pb.root_of, S.pb.agg_size, S.f, S.g))) return st;
@@ -138,8 +138,10 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
         // setup scratch, sized for level 0 (every coarser graph is smaller)
         Scratch S;
         S.pb.state = dalloc<uint8_t>(h, n0, &st, true);
-        S.pb.b1 = dalloc<uint64_t>(h, n0, &st, true);
+        S.pb.b1 = dalloc<uint64_t>(h, 2 * (size_t)n0, &st, true);
         S.pb.blocked = dalloc<uint8_t>(h, n0, &st, true);
+        S.pb.list = dalloc<int>(h, 2 * (size_t)n0, &st, true);
+        S.pb.cprio = dalloc<uint64_t>(h, n0, &st, true);
         S.pb.root_of = dalloc<int>(h, n0, &st, true);
         S.pb.agg_size = dalloc<int>(h, n0, &st, true);
         S.pb.slots = dalloc<int>(h, kMaxRoundSlots, &st, true);

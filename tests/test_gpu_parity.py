@@ -5,7 +5,8 @@ Bars (stated per test):
   * priorities, aggregation passes, aggregates, coarse numbering: bit-exact;
   * coarse matrices and the l1-Jacobi diagonal: bit-exact for every weight (both sides add
     the same terms in the same order, Eq. 2.4 / Section 4.1);
-  * the two-level operator B (no inner products): FP64 relative 1e-12;
+  * the two-level operator B (no inner products): FP64 relative max(1e-12, eps cond(A_c)),
+    as the two sides invert the coarsest matrix by different backward-stable methods;
   * K-cycle and solves: both reach the stated relative residual, the FP64 path within +-1
     iteration of the oracle, and |A (x_gpu - x_oracle)| <= 2 tol |b| (implied by both
     residuals, checked on the host in FP64).
@@ -124,6 +125,15 @@ def test_long_rows_cross_chunks(oracle):
         U.uaamg_free(h)
 
 
+def coarse_solve_bar(H):
+    """FP64 bar for an operator that applies the exact coarsest solve: the two sides invert
+    A_c by different backward-stable methods (Gauss-Jordan on the GPU, Cholesky in the
+    oracle), whose solutions may each be off by about eps * cond(A_c) relative."""
+    rp, c, v = H.csr(H.num_levels - 1)
+    Ac = sp.csr_matrix((v, c, rp)).toarray()
+    return max(1e-12, np.finfo(float).eps * np.linalg.cond(Ac))
+
+
 def test_two_level_operator_fp64(oracle):
     A = I.grid2d(40, 37)
     for pre, post in ((1, 1), (2, 2), (0, 1), (1, 0), (3, 2)):
@@ -133,7 +143,7 @@ def test_two_level_operator_fp64(oracle):
             r = np.random.default_rng(pre * 7 + post).standard_normal(A.n)
             g = U.uaamg_apply_B(h, 0, r)
             o = H.apply_B(0, r)
-            assert np.linalg.norm(g - o) <= 1e-12 * np.linalg.norm(o), (pre, post)
+            assert np.linalg.norm(g - o) <= coarse_solve_bar(H) * np.linalg.norm(o), (pre, post)
         finally:
             U.uaamg_free(h)
 
@@ -171,11 +181,11 @@ def test_tma_rowblock_path(oracle, precision):
     wD = np.zeros(n)
     wD[n - 1] = 1.0
     cases = [I.grid2d(40, 37), I.laplacian_from_edges(n, ei, ej, w, wD)]
-    tol_b = 1e-12 if precision == U.UAAMG_FP64 else 2e-5
     for A in cases:
         h, H, _ = both(A, oracle, precision=precision, max_levels=2, coarse_size=64,
                        max_agg_size=0, agg_repeat=2, tma_rows=1)
         try:
+            tol_b = coarse_solve_bar(H) if precision == U.UAAMG_FP64 else 2e-5
             r = np.random.default_rng(4).standard_normal(A.n)
             g, o = U.uaamg_apply_B(h, 0, r), H.apply_B(0, r)
             assert np.linalg.norm(g - o) <= tol_b * np.linalg.norm(o)
@@ -292,6 +302,35 @@ def test_solve_edge_cases(oracle):
     finally:
         U.uaamg_free(h)
 
+
+
+@pytest.mark.parametrize("n_side,coarse", [(8, 64), (7, 64), (32, 1024), (31, 1024)])
+def test_single_level_dense_inverse(n_side, coarse):
+    """A single level inverted densely: even and odd n (the inversion alternates two
+    buffers per step) up to the 1024 limit; FP64 solve exact to 1e-12 in one iteration."""
+    A = I.grid2d(n_side)
+    h = U.uaamg_setup(A.rowptr, A.col, A.val,
+                      U.uaamg_default_params(precision=U.UAAMG_FP64, coarse_size=coarse))
+    try:
+        assert U.uaamg_num_levels(h) == 1
+        b = I.rhs_uniform(A.n, 6)
+        x = np.zeros(A.n)
+        st, it, rr = U.uaamg_solve(h, b, x, 1e-12)
+        assert st == 0 and it == 1 and rr < 1e-12
+        xs = np.linalg.solve(A.dense(), b)
+        assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+    finally:
+        U.uaamg_free(h)
+
+
+def test_indefinite_coarsest_is_reported():
+    """Symmetric, positive diagonal, but indefinite: the second pivot is 1 - 4 < 0."""
+    rp = np.array([0, 2, 4, 5], dtype=np.int32)
+    col = np.array([0, 1, 0, 1, 2], dtype=np.int32)
+    val = np.array([1.0, -2.0, -2.0, 1.0, 1.0])
+    with pytest.raises(U.UaamgError) as e:
+        U.uaamg_setup(rp, col, val)
+    assert e.value.status == 3
 
 def test_bad_csr_is_rejected():
     A = I.grid2d(12)
