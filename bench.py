@@ -34,14 +34,25 @@ WORKLOAD = "laplace3d_128^3 7-point, Dirichlet, lognormal(0.25) edge weights"
 # weaker than 5x, and a small level that shrinks by less than 1.5x becomes the coarsest.
 BENCH_PARAMS = dict(max_agg_size=4, agg_repeat=2, kcycle_ratio=5.0, min_coarsening=1.5)
 
-# DRAM traffic per launch of the roofline kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {}
+# DRAM traffic per launch of each roofline kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the sources that
+# define that kernel: it reads as null once any of them changes.
+NCU_SOURCES = {
+    "smooth0": ("kern_tma.cu", "kernels.cuh", "common.cuh"),
+    "spmv64": ("kern_tma.cu", "kernels.cuh", "common.cuh"),
+    "paa": ("kern_setup.cu", "kernels.cuh", "common.cuh"),
+    "coarse": ("kern_setup.cu", "kernels.cuh", "common.cuh"),
+}
+NCU_TRAFFIC = {
+    # k_rowblock_tma<float, RB_PRE1> on level 0 of the 128^3 system, ncu --set full
+    # (profiles/rowblock_tma_laplace3d_128_level0.md): 141,838,336 + 8,989,952 bytes
+    ("smooth0", "2ef10e578243be6c"): 150828288,
+}
 
 
-def _src_hash() -> str:
+def _src_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in ("kern_solve.cu", "kern_setup.cu", "common.cuh"):
+    for f in NCU_SOURCES.get(kernel, ()):
         h.update(open(os.path.join(ROOT, "paper_1302_2547_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -297,7 +308,7 @@ def run_gpu(args, rank, world):
     if n_launch and ms_launch > 0:
         avg_s = ms_launch / n_launch / 1000.0
         achieved = bytes_launch / avg_s / 1e9
-        traffic = NCU_TRAFFIC.get((args.roofline_kernel, _src_hash()))
+        traffic = NCU_TRAFFIC.get((args.roofline_kernel, _src_hash(args.roofline_kernel)))
         roof = {"bound": "hbm", "kernel": args.roofline_kernel, "achieved": round(achieved, 1),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
