@@ -47,6 +47,7 @@ static void destroy(Handle* h) {
     if (!h) return;
     if (h->work) cudaStreamSynchronize(h->work);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->loop_graph) cudaGraphExecDestroy(h->loop_graph);
     if (h->mgraph) cudaGraphExecDestroy(h->mgraph);
     if (h->mos_host) cudaFreeHost(h->mos_host);
     for (auto& ps : h->prof_slots) {

@@ -48,6 +48,10 @@ struct LevelScalars {
     double rho1, alpha1, beta, gamma, alpha2, rtrt, rhorho;
     int skip2;  // 1 when this level's second step is skipped
     int pad;
+    // derived once by the last block of the reduction that completes their inputs (per-thread
+    // FP64 divisions would make the element-wise kernels FP64-bound):
+    //   a1 = alpha1 / rho1 (0 when rho1 <= 0); e = w1 c1 + w2 c2
+    double a1, w1, w2;
 };
 
 // FP64 scalars of the outer flexible CG.
@@ -60,6 +64,14 @@ struct OuterScalars {
     double alpha;
     int first;      // 1 until the first direction update
     int breakdown;  // (p, A p) <= 0 seen
+    // device-side iteration loop: stop once rr <= stop_rr, after it_limit iterations or on
+    // breakdown; it counts the iterations of the current launch
+    double stop_rr;
+    int it;
+    int it_limit;
+    // this iteration's step sizes, derived once by the reductions that complete them
+    double beta_cur;   // (z, q) / (p, q)_prev, 0 on the first iteration
+    double alpha_cur;  // (p, r) / (p, A p), 0 when (p, A p) <= 0
 };
 
 struct Level {
@@ -138,6 +150,13 @@ struct Handle {
     // graph of one outer iteration
     cudaGraphExec_t graph = nullptr;
     long long graph_nodes = 0;
+    // graph of the whole iteration loop (a while node around one iteration; the condition is
+    // set on the device), its kernel count per iteration and the relative residual per
+    // iteration it writes
+    cudaGraphExec_t loop_graph = nullptr;
+    long long loop_nodes = 0;
+    double* d_hist = nullptr;
+    int hist_cap = 0;
     // stats
     double setup_ms = 0, solve_ms = 0;
     long long launches = 0;
@@ -217,9 +236,10 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* c) {
 
 // Deterministic reduction of ND per-thread values over the whole grid: each block reduces
 // with a fixed tree and stores its partials; the last block to arrive adds the partials in
-// block order and writes result[0..ND).  Every thread of every block must call it.
+// block order and writes result[0..ND).  Every thread of every block must call it.  Returns
+// true only in thread 0 of the last block, once result is written.
 template <int ND>
-__device__ __forceinline__ void grid_reduce(const double (&v)[ND], double* partials,
+__device__ __forceinline__ bool grid_reduce(const double (&v)[ND], double* partials,
                                             unsigned int* counter, double* result) {
     __shared__ double sh[ND][kThreads / 32];
     __shared__ bool is_last;
@@ -242,7 +262,7 @@ __device__ __forceinline__ void grid_reduce(const double (&v)[ND], double* parti
         is_last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!is_last) return;
+    if (!is_last) return false;
     __threadfence();
     double acc[ND];
 #pragma unroll
@@ -267,6 +287,7 @@ __device__ __forceinline__ void grid_reduce(const double (&v)[ND], double* parti
         }
         *counter = 0u;
     }
+    return threadIdx.x == 0;  // thread 0 of the last block, after result is written
 }
 
 // Rounded arithmetic without contraction, so that FP64 epilogues round exactly like the

@@ -11,6 +11,8 @@
 
 namespace uaamg {
 
+constexpr int kMColMax = 32;  // most right-hand sides one multi-vector call carries
+
 struct MGeom {
     int R, Rp, lgRp, rows_per_block;
 };
@@ -111,16 +113,16 @@ __global__ void __launch_bounds__(kThreads) k_mrow(MArgs<T> a) {
         } else if constexpr (MODE == RB_RESID) {
             const T yi = sub_rn(a.r[o], acc);
             a.y[o] = yi;
-            if constexpr (ND >= 1) dv[0] += (double)yi * (double)yi;
+            if constexpr (ND >= 1) dv[0] = fma((double)yi, (double)yi, dv[0]);
         } else if constexpr (MODE == RB_PROSMOOTH) {
             const T xi = add_rn(a.x[o], a.e[(size_t)a.agg[i] * R + lr]);
             a.y[o] = add_rn(xi, mul_rn(a.minv[i], sub_rn(a.r[o], acc)));
         } else {
             a.y[o] = acc;
             const double xi = (double)a.x[o];
-            if constexpr (ND >= 1) dv[0] += xi * (double)acc;
-            if constexpr (ND >= 2) dv[1] += xi * (double)a.d1[o];
-            if constexpr (ND >= 3) dv[2] += xi * (double)a.d2[o];
+            if constexpr (ND >= 1) dv[0] = fma(xi, (double)acc, dv[0]);
+            if constexpr (ND >= 2) dv[1] = fma(xi, (double)a.d1[o], dv[1]);
+            if constexpr (ND >= 3) dv[2] = fma(xi, (double)a.d2[o], dv[2]);
         }
     }
     if constexpr (ND > 0) grid_reduce_cols<ND>(dv, g, a.partials, a.counter, a.result);
@@ -205,8 +207,13 @@ k_mkc_rt(int n, int R, const T* __restrict__ rho, const T* __restrict__ v1, T* _
     const MGeom g = mgeom(R);
     const int lr = threadIdx.x & (g.Rp - 1);
     double dv[2] = {0.0, 0.0};
-    const double rho1 = lr < R ? sc[lr] : 0.0, alpha1 = lr < R ? sc[R + lr] : 0.0;
-    const T a1 = (T)(rho1 > 0.0 ? alpha1 / rho1 : 0.0);
+    __shared__ double sa1[kMColMax];  // alpha1 / rho1 per column, once per block
+    if ((int)threadIdx.x < R) {
+        const double rho1 = sc[threadIdx.x], alpha1 = sc[R + threadIdx.x];
+        sa1[threadIdx.x] = rho1 > 0.0 ? alpha1 / rho1 : 0.0;
+    }
+    __syncthreads();
+    const T a1 = (T)(lr < R ? sa1[lr] : 0.0);
     for (int i = blockIdx.x * g.rows_per_block + (threadIdx.x >> g.lgRp); i < n;
          i += gridDim.x * g.rows_per_block) {
         if (lr >= R) continue;
@@ -214,8 +221,8 @@ k_mkc_rt(int n, int R, const T* __restrict__ rho, const T* __restrict__ v1, T* _
         const T v = sub_rn(rho[o], mul_rn(a1, v1[o]));
         rt[o] = v;
         if constexpr (TAU) {
-            dv[0] += (double)v * (double)v;
-            dv[1] += (double)rho[o] * (double)rho[o];
+            dv[0] = fma((double)v, (double)v, dv[0]);
+            dv[1] = fma((double)rho[o], (double)rho[o], dv[1]);
         }
     }
     if constexpr (TAU) grid_reduce_cols<2>(dv, g, partials, counter, sc + 5 * R);
@@ -228,22 +235,30 @@ k_mkc_combine(int n, int R, const T* __restrict__ c1, const T* __restrict__ c2,
     const MGeom g = mgeom(R);
     const int lr = threadIdx.x & (g.Rp - 1);
     const int i = blockIdx.x * g.rows_per_block + (threadIdx.x >> g.lgRp);
-    if (i >= n || lr >= R) return;
-    const double rho1 = sc[lr], alpha1 = sc[R + lr];
-    double w1 = 0.0, w2 = 0.0;
-    if (rho1 > 0.0) {
-        w1 = alpha1 / rho1;
-        bool two = second != 0;
-        if (two && tau > 0.0 && sqrt(sc[5 * R + lr]) <= tau * sqrt(sc[6 * R + lr])) two = false;
-        if (two) {
-            const double beta = sc[2 * R + lr], gamma = sc[3 * R + lr], alpha2 = sc[4 * R + lr];
-            const double rho2 = beta - gamma * gamma / rho1;
-            if (rho2 > 0.0) {
-                w1 = w1 - gamma * alpha2 / (rho1 * rho2);
-                w2 = alpha2 / rho2;
+    __shared__ double sw[2][kMColMax];  // the column's weights, once per block
+    if ((int)threadIdx.x < R) {
+        const int c = threadIdx.x;
+        const double rho1 = sc[c], alpha1 = sc[R + c];
+        double w1 = 0.0, w2 = 0.0;
+        if (rho1 > 0.0) {
+            w1 = alpha1 / rho1;
+            bool two = second != 0;
+            if (two && tau > 0.0 && sqrt(sc[5 * R + c]) <= tau * sqrt(sc[6 * R + c])) two = false;
+            if (two) {
+                const double beta = sc[2 * R + c], gamma = sc[3 * R + c], alpha2 = sc[4 * R + c];
+                const double rho2 = beta - gamma * gamma / rho1;
+                if (rho2 > 0.0) {
+                    w1 = w1 - gamma * alpha2 / (rho1 * rho2);
+                    w2 = alpha2 / rho2;
+                }
             }
         }
+        sw[0][c] = w1;
+        sw[1][c] = w2;
     }
+    __syncthreads();
+    if (i >= n || lr >= R) return;
+    const double w1 = sw[0][lr], w2 = sw[1][lr];
     const size_t o = (size_t)i * R + lr;
     T v = mul_rn((T)w1, c1[o]);
     if (w2 != 0.0) v = add_rn(v, mul_rn((T)w2, c2[o]));
@@ -295,7 +310,7 @@ k_mzq(int n, int R, const T* __restrict__ z, const double* __restrict__ q, doubl
     for (int i = i0; i < n; i += gridDim.x * g.rows_per_block) {
         if (lr >= R) continue;
         const size_t o = (size_t)i * R + lr;
-        dv[0] += (double)z[o] * q[o];
+        dv[0] = fma((double)z[o], q[o], dv[0]);
     }
     grid_reduce_cols<1>(dv, g, partials, counter, os + 2 * R);
 }
@@ -303,11 +318,16 @@ k_mzq(int n, int R, const T* __restrict__ z, const double* __restrict__ q, doubl
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_mp(long long m, int R, const T* __restrict__ z, double* __restrict__ p, const double* os) {
+    __shared__ double sb[kMColMax];  // beta per column, once per block
+    if ((int)threadIdx.x < R) {
+        const int c = threadIdx.x;
+        sb[c] = (os[7 * R + c] != 0.0) ? 0.0 : os[2 * R + c] / os[5 * R + c];
+    }
+    __syncthreads();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m) return;
-    const int r = (int)(t % R);
-    const double beta = (os[7 * R + r] != 0.0) ? 0.0 : os[2 * R + r] / os[5 * R + r];
-    p[t] = __dsub_rn((double)z[t], __dmul_rn(beta, p[t]));
+    const double beta = sb[(int)(t % R)];
+    p[t] = fma(-beta, p[t], (double)z[t]);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -317,15 +337,21 @@ k_mxr(int n, int R, double* __restrict__ x, double* __restrict__ r, const double
     const int lr = threadIdx.x & (g.Rp - 1);
     const int i0 = blockIdx.x * g.rows_per_block + (threadIdx.x >> g.lgRp);
     double dv[1] = {0.0};
-    const double pq = lr < R ? os[lr] : 0.0, active = lr < R ? os[6 * R + lr] : 0.0;
-    const double alpha = (active != 0.0 && pq > 0.0) ? os[R + lr] / pq : 0.0;
+    __shared__ double sal[kMColMax];  // alpha per column, once per block
+    if ((int)threadIdx.x < R) {
+        const int c = threadIdx.x;
+        const double pq = os[c], active = os[6 * R + c];
+        sal[c] = (active != 0.0 && pq > 0.0) ? os[R + c] / pq : 0.0;
+    }
+    __syncthreads();
+    const double alpha = lr < R ? sal[lr] : 0.0;
     for (int i = i0; i < n; i += gridDim.x * g.rows_per_block) {
         if (lr >= R) continue;
         const size_t o = (size_t)i * R + lr;
-        x[o] = __dadd_rn(x[o], __dmul_rn(alpha, p[o]));
-        const double ri = __dsub_rn(r[o], __dmul_rn(alpha, q[o]));
+        x[o] = fma(alpha, p[o], x[o]);
+        const double ri = fma(-alpha, q[o], r[o]);
         r[o] = ri;
-        dv[0] += ri * ri;
+        dv[0] = fma(ri, ri, dv[0]);
     }
     grid_reduce_cols<1>(dv, g, partials, counter, os + 3 * R);
 }
@@ -375,7 +401,7 @@ k_mnorm(int n, int R, const double* __restrict__ b, double* out, double* partial
     for (int i = i0; i < n; i += gridDim.x * g.rows_per_block) {
         if (lr >= R) continue;
         const double v = b[(size_t)i * R + lr];
-        dv[0] += v * v;
+        dv[0] = fma(v, v, dv[0]);
     }
     grid_reduce_cols<1>(dv, g, partials, counter, out);
 }

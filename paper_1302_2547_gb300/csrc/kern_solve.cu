@@ -40,7 +40,8 @@ constexpr int kGrp = 2;  // four-entry groups a thread loads per batch
 
 template <typename T, int MODE, int ND>
 __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
-    if (a.skip && *(volatile const int*)a.skip) return;
+    if (!rb_enter<T, MODE>(a)) return;
+    const KScal<T> ks = kscal<T, MODE>(a);
     __shared__ T sval[kChunk];
     __shared__ T sx[kChunk];
     const int lanes = kRowsPerBlock / a.rows;  // threads per row: 1, 2, 4 or 8
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
                     const int k = kb0 + g * 4 * kThreads + e;
-                    xg[g][e] = (k >= c0 && k < c1) ? rb_gather<T, MODE>(a, j[g][e]) : T(0);
+                    xg[g][e] = (k >= c0 && k < c1) ? rb_gather<T, MODE>(a, ks, j[g][e]) : T(0);
                 }
 #pragma unroll
             for (int g = 0; g < kGrp; g++)
@@ -118,6 +119,11 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
         if constexpr (MODE == RB_PRE1) {
             a.y[i] = mul_rn(a.minv[i], a.r[i]);
             a.y2[i] = sub_rn(a.r[i], acc);
+        } else if constexpr (MODE == RB_PRE1_RT) {
+            const T ri = kc_rt_at(a, ks, i);
+            a.y[i] = mul_rn(a.minv[i], ri);
+            a.y2[i] = sub_rn(ri, acc);
+            a.y3[i] = ri;
         } else if constexpr (MODE == RB_SMOOTH) {
             a.y[i] = add_rn(a.x[i], mul_rn(a.minv[i], sub_rn(a.r[i], acc)));
         } else if constexpr (MODE == RB_RESID) {
@@ -127,6 +133,9 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
         } else if constexpr (MODE == RB_PROSMOOTH) {
             const T xi = add_rn(a.x[i], a.e[a.agg[i]]);
             a.y[i] = add_rn(xi, mul_rn(a.minv[i], sub_rn(a.r[i], acc)));
+        } else if constexpr (MODE == RB_PROSMOOTH_E) {
+            const T xi = add_rn(a.x[i], kc_e_at(a, ks, a.agg[i]));
+            a.y[i] = add_rn(xi, mul_rn(a.minv[i], sub_rn(a.r[i], acc)));
         } else {  // RB_SPMV
             a.y[i] = acc;
             const double xi = (double)a.x[i];
@@ -135,7 +144,9 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
             if constexpr (ND >= 3) dv[2] = xi * (double)a.d2[i];
         }
     }
-    if constexpr (ND > 0) grid_reduce<ND>(dv, a.partials, a.counter, a.result);
+    if constexpr (ND > 0) {
+        if (grid_reduce<ND>(dv, a.partials, a.counter, a.result)) rb_last_block(a);
+    }
 }
 
 template <typename T>
@@ -151,6 +162,8 @@ int launch_rowblock(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
         return check_cuda(cudaGetLastError());                        \
     }
     RB_CASE(RB_PRE1, 0)
+    RB_CASE(RB_PRE1_RT, 0)
+    RB_CASE(RB_PROSMOOTH_E, 0)
     RB_CASE(RB_SMOOTH, 0)
     RB_CASE(RB_RESID, 0)
     RB_CASE(RB_RESID, 1)
@@ -232,10 +245,8 @@ __global__ void __launch_bounds__(kThreads)
 k_kc_rt(int level, int n, const T* __restrict__ rho, const T* __restrict__ v1, T* __restrict__ rt,
         LevelScalars* sc, int inner, double tau, Ctrl* ctrl, double* partials) {
     if (*(volatile const int*)&ctrl->skip) return;
-    const double rho1 = sc->rho1, alpha1 = sc->alpha1;
-    const bool ok = rho1 > 0.0;
-    const double a1 = ok ? alpha1 / rho1 : 0.0;
-    const T a1t = (T)a1;
+    const bool ok = sc->rho1 > 0.0;
+    const T a1t = (T)sc->a1;  // alpha1 / rho1, set by the first SpMV's last block
     double dv[2] = {0.0, 0.0};
     const int gs = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
@@ -289,19 +300,7 @@ k_kc_combine(int level, int n, const T* __restrict__ c1, const T* __restrict__ c
              T* __restrict__ e, const LevelScalars* sc, Ctrl* ctrl) {
     const int sk = *(volatile const int*)&ctrl->skip;
     if (sk != 0 && sk != level + 1) return;  // inside an ancestor's skipped step
-    const double rho1 = sc->rho1, alpha1 = sc->alpha1;
-    double w1 = 0.0, w2 = 0.0;
-    if (rho1 > 0.0) {
-        w1 = alpha1 / rho1;
-        if (!sc->skip2) {
-            const double gamma = sc->gamma, beta = sc->beta, alpha2 = sc->alpha2;
-            const double rho2 = beta - gamma * gamma / rho1;
-            if (rho2 > 0.0) {
-                w1 = w1 - gamma * alpha2 / (rho1 * rho2);
-                w2 = alpha2 / rho2;
-            }
-        }
-    }
+    const double w1 = sc->w1, w2 = sc->w2;    // set by the step SpMVs' last blocks
     const T w1t = (T)w1, w2t = (T)w2;
     const bool two = (w2 != 0.0);
     const int gs = gridDim.x * blockDim.x;
@@ -378,15 +377,18 @@ int launch_cast_d2f(Handle* h, int n, const double* in, float* out) {
     return check_cuda(cudaGetLastError());
 }
 
+// result = (a, b).  With osc: result is (z, q) of the outer iteration, and the last block
+// also derives beta = (z, q) / (p, q)_prev once for the direction update.
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(kThreads)
 k_dot(int n, const TA* __restrict__ a, const TB* __restrict__ b, double* partials,
-      unsigned int* counter, double* result) {
+      unsigned int* counter, double* result, OuterScalars* osc) {
     double dv[1] = {0.0};
     const int gs = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs)
-        dv[0] += (double)a[i] * (double)b[i];
-    grid_reduce<1>(dv, partials, counter, result);
+        dv[0] = fma((double)a[i], (double)b[i], dv[0]);
+    if (grid_reduce<1>(dv, partials, counter, result) && osc)
+        osc->beta_cur = osc->first ? 0.0 : result[0] / osc->pq_prev;
 }
 
 static int dot_grid(Handle* h, int n) {
@@ -395,14 +397,14 @@ static int dot_grid(Handle* h, int n) {
 }
 
 int launch_dot(Handle* h, int n, const double* a, const double* b, double* result) {
-    k_dot<double, double><<<dot_grid(h, n), kThreads, 0, h->work>>>(n, a, b, h->partials, &h->ctrl->red_count, result);
+    k_dot<double, double><<<dot_grid(h, n), kThreads, 0, h->work>>>(n, a, b, h->partials, &h->ctrl->red_count, result, nullptr);
     count_launch(h);
     return check_cuda(cudaGetLastError());
 }
 
 template <typename T>
 int launch_outer_zq(Handle* h, int n, const T* z, const double* q, OuterScalars* osc) {
-    k_dot<T, double><<<dot_grid(h, n), kThreads, 0, h->work>>>(n, z, q, h->partials, &h->ctrl->red_count, &osc->zq);
+    k_dot<T, double><<<dot_grid(h, n), kThreads, 0, h->work>>>(n, z, q, h->partials, &h->ctrl->red_count, &osc->zq, osc);
     count_launch(h);
     return check_cuda(cudaGetLastError());
 }
@@ -412,9 +414,9 @@ template int launch_outer_zq<double>(Handle*, int, const double*, const double*,
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_outer_p(int n, const T* __restrict__ z, double* __restrict__ p, const OuterScalars* osc) {
-    const double beta = osc->first ? 0.0 : osc->zq / osc->pq_prev;
+    const double beta = osc->beta_cur;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = __dsub_rn((double)z[i], __dmul_rn(beta, p[i]));
+    if (i < n) p[i] = fma(-beta, p[i], (double)z[i]);
 }
 
 template <typename T>
@@ -432,14 +434,14 @@ k_outer_xr(int n, double* __restrict__ x, double* __restrict__ r, const double* 
            unsigned int* counter) {
     const double pq = osc->pq;
     const bool ok = pq > 0.0;
-    const double alpha = ok ? osc->pr / pq : 0.0;
+    const double alpha = osc->alpha_cur;  // set by the outer SpMV's last block
     double dv[1] = {0.0};
     const int gs = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gs) {
-        x[i] = __dadd_rn(x[i], __dmul_rn(alpha, p[i]));
-        const double ri = __dsub_rn(r[i], __dmul_rn(alpha, q[i]));
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
-        dv[0] += ri * ri;
+        dv[0] = fma(ri, ri, dv[0]);
     }
     grid_reduce<1>(dv, partials, counter, &osc->rr);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -454,6 +456,23 @@ k_outer_xr(int n, double* __restrict__ x, double* __restrict__ r, const double* 
 int launch_outer_xr(Handle* h, int n, double* x, double* r, const double* p, const double* q,
                     OuterScalars* osc) {
     k_outer_xr<<<dot_grid(h, n), kThreads, 0, h->work>>>(n, x, r, p, q, osc, h->partials, &h->ctrl->red_count);
+    count_launch(h);
+    return check_cuda(cudaGetLastError());
+}
+
+// End of one iteration of the device-side loop (one thread): count it, record the relative
+// residual, and decide whether the loop's body runs again.
+__global__ void k_outer_loop(OuterScalars* osc, double* hist, int hist_cap,
+                             cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int k = ++osc->it;
+    if (k < hist_cap) hist[k] = sqrt(osc->rr / osc->bb);
+    const bool more = !osc->breakdown && osc->rr > osc->stop_rr && k < osc->it_limit;
+    cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
+int launch_outer_loop(Handle* h, cudaGraphConditionalHandle cond) {
+    k_outer_loop<<<1, 32, 0, h->work>>>(h->osc, h->d_hist, h->hist_cap, cond);
     count_launch(h);
     return check_cuda(cudaGetLastError());
 }

@@ -78,15 +78,15 @@ __device__ __forceinline__ bool tma_issue(const RBArgs<T>& a, TmaSmem<T>& sm, in
 // One row's sum over entries [lo, hi) of col/val, in stored order; the vector entries of
 // kTmaBatch entries are gathered before the first is used.
 template <typename T, int MODE>
-__device__ __forceinline__ T row_sum(const RBArgs<T>& a, const int* col, const T* val, int lo,
-                                     int hi) {
+__device__ __forceinline__ T row_sum(const RBArgs<T>& a, const KScal<T>& ks, const int* col,
+                                     const T* val, int lo, int hi) {
     T acc = T(0);
     for (int k = lo; k < hi; k += kTmaBatch) {
         T xg[kTmaBatch], vv[kTmaBatch];
 #pragma unroll
         for (int u = 0; u < kTmaBatch; u++) {
             const bool in = k + u < hi;
-            xg[u] = in ? rb_gather<T, MODE>(a, col[k + u]) : T(0);
+            xg[u] = in ? rb_gather<T, MODE>(a, ks, col[k + u]) : T(0);
             vv[u] = in ? val[k + u] : T(0);
         }
 #pragma unroll
@@ -98,7 +98,8 @@ __device__ __forceinline__ T row_sum(const RBArgs<T>& a, const int* col, const T
 
 template <typename T, int MODE, int ND>
 __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ctrl) {
-    if (a.skip && *(volatile const int*)a.skip) return;
+    if (!rb_enter<T, MODE>(a)) return;
+    const KScal<T> ks = kscal<T, MODE>(a);
     extern __shared__ __align__(128) unsigned char dyn[];
     TmaSmem<T>& sm = *reinterpret_cast<TmaSmem<T>*>(dyn);
     __shared__ int staged[2];  // 1 when the stage holds its row block's entries
@@ -142,14 +143,14 @@ __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ct
         if (row < r1) {  // per-row operands, loaded before waiting on the stage
             rs = a.rowptr[row];
             re = a.rowptr[row + 1];
-            if constexpr (MODE == RB_PRE1 || MODE == RB_SMOOTH || MODE == RB_PROSMOOTH ||
-                          MODE == RB_RESID)
+            constexpr bool pro = MODE == RB_PROSMOOTH || MODE == RB_PROSMOOTH_E;
+            if constexpr (MODE == RB_PRE1_RT) ri = kc_rt_at(a, ks, row);
+            else if constexpr (MODE == RB_PRE1 || MODE == RB_SMOOTH || pro || MODE == RB_RESID)
                 ri = a.r[row];
-            if constexpr (MODE == RB_PRE1 || MODE == RB_SMOOTH || MODE == RB_PROSMOOTH)
+            if constexpr (MODE == RB_PRE1 || MODE == RB_PRE1_RT || MODE == RB_SMOOTH || pro)
                 mi = a.minv[row];
-            if constexpr (MODE == RB_SMOOTH || MODE == RB_PROSMOOTH || MODE == RB_SPMV)
-                xi = a.x[row];
-            if constexpr (MODE == RB_PROSMOOTH) gi = a.agg[row];
+            if constexpr (MODE == RB_SMOOTH || pro || MODE == RB_SPMV) xi = a.x[row];
+            if constexpr (pro) gi = a.agg[row];
         }
         T acc = T(0);
         if (staged[s]) {
@@ -177,30 +178,37 @@ __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ct
                 return;
             }
             phase ^= 1u << s;
-            if (row < r1) acc = row_sum<T, MODE>(a, sm.col[s], sm.val[s], rs - a0, re - a0);
+            if (row < r1) acc = row_sum<T, MODE>(a, ks, sm.col[s], sm.val[s], rs - a0, re - a0);
         } else if (row < r1) {  // entries beyond a stage: straight from global memory
-            acc = row_sum<T, MODE>(a, a.col, a.val, rs, re);
+            acc = row_sum<T, MODE>(a, ks, a.col, a.val, rs, re);
         }
         if (row < r1) {
             const int i = row;
             if constexpr (MODE == RB_PRE1) {
                 a.y[i] = mul_rn(mi, ri);
                 a.y2[i] = sub_rn(ri, acc);
+            } else if constexpr (MODE == RB_PRE1_RT) {
+                a.y[i] = mul_rn(mi, ri);
+                a.y2[i] = sub_rn(ri, acc);
+                a.y3[i] = ri;
             } else if constexpr (MODE == RB_SMOOTH) {
                 a.y[i] = add_rn(xi, mul_rn(mi, sub_rn(ri, acc)));
             } else if constexpr (MODE == RB_RESID) {
                 const T yi = sub_rn(ri, acc);
                 a.y[i] = yi;
-                if constexpr (ND >= 1) dv[0] += (double)yi * (double)yi;
+                if constexpr (ND >= 1) dv[0] = fma((double)yi, (double)yi, dv[0]);
             } else if constexpr (MODE == RB_PROSMOOTH) {
                 const T xp = add_rn(xi, a.e[gi]);
+                a.y[i] = add_rn(xp, mul_rn(mi, sub_rn(ri, acc)));
+            } else if constexpr (MODE == RB_PROSMOOTH_E) {
+                const T xp = add_rn(xi, kc_e_at(a, ks, gi));
                 a.y[i] = add_rn(xp, mul_rn(mi, sub_rn(ri, acc)));
             } else {
                 a.y[i] = acc;
                 const double xd = (double)xi;
-                if constexpr (ND >= 1) dv[0] += xd * (double)acc;
-                if constexpr (ND >= 2) dv[1] += xd * (double)a.d1[i];
-                if constexpr (ND >= 3) dv[2] += xd * (double)a.d2[i];
+                if constexpr (ND >= 1) dv[0] = fma(xd, (double)acc, dv[0]);
+                if constexpr (ND >= 2) dv[1] = fma(xd, (double)a.d1[i], dv[1]);
+                if constexpr (ND >= 3) dv[2] = fma(xd, (double)a.d2[i], dv[2]);
             }
         }
         // Stage s is free once every thread is past this barrier.  staged[s] is read next
@@ -208,7 +216,9 @@ __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ct
         __syncthreads();
         if (threadIdx.x == 0) staged[s] = (nrb < nblk) ? (tma_issue<T>(a, sm, nk0, nk1, s) ? 1 : 0) : 0;
     }
-    if constexpr (ND > 0) grid_reduce<ND>(dv, a.partials, a.counter, a.result);
+    if constexpr (ND > 0) {
+        if (grid_reduce<ND>(dv, a.partials, a.counter, a.result)) rb_last_block(a);
+    }
 }
 
 template <typename T, int MODE, int ND>
@@ -236,6 +246,8 @@ int launch_rowblock_tma(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
 #define TMA_CASE(M, D) \
     if (mode == M && ndots == D) return launch_one<T, M, D>(h, a);
     TMA_CASE(RB_PRE1, 0)
+    TMA_CASE(RB_PRE1_RT, 0)
+    TMA_CASE(RB_PROSMOOTH_E, 0)
     TMA_CASE(RB_SMOOTH, 0)
     TMA_CASE(RB_RESID, 0)
     TMA_CASE(RB_RESID, 1)

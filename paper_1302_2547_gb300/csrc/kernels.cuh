@@ -50,12 +50,22 @@ int launch_dense_coarsest(Handle* h, int n, const int* rowptr, const int* col,
 // ---- solve (kern_solve.cu) --------------------------------------------------------------
 // Row-block CSR kernels (Section 4.4 SpMV fused with the Section 4.1 smoother).
 enum RBMode {
-    RB_PRE1 = 0,      // x = Minv r (first sweep from zero); s = r - A x
-    RB_SMOOTH = 1,    // y = x + Minv (r - A x)
-    RB_RESID = 2,     // y = r - A x          (optional dot (y, y))
-    RB_PROSMOOTH = 3, // xp = x + P e; y = xp + Minv (r - A xp)
-    RB_SPMV = 4,      // y = A x              (dots (x, y), (x, d1), (x, d2))
+    RB_PRE1 = 0,        // x = Minv r (first sweep from zero); s = r - A x
+    RB_SMOOTH = 1,      // y = x + Minv (r - A x)
+    RB_RESID = 2,       // y = r - A x          (optional dot (y, y))
+    RB_PROSMOOTH = 3,   // xp = x + P e; y = xp + Minv (r - A xp)
+    RB_SPMV = 4,        // y = A x              (dots (x, y), (x, d1), (x, d2))
+    RB_PRE1_RT = 5,     // RB_PRE1 with r = rho~ = rho - a1 v1 formed on the fly; writes rho~
+    RB_PROSMOOTH_E = 6, // RB_PROSMOOTH with e = w1 c1 + w2 c2 formed on the fly
 };
+// Arguments of the row-block kernels.  The two fused modes take over the element-wise K-cycle
+// steps (Section 4.3) with the same arithmetic per entry:
+//   RB_PRE1_RT reads r = rho (the coarse right-hand side), d1 = v1 and rsc (a1 = alpha1/rho1)
+//     and writes rho~ to y3;
+//   RB_PROSMOOTH_E reads e = c1, e2 = c2 and esc (w1, w2) of coarse level elevel, and clears
+//     that level's skip value (elevel + 1) in skip_rw.
+// ksc != null on the first SpMV of a K-cycle step: its last block, once rho1 is summed,
+// decides whether level klevel takes a second step (kinner = steps allowed).
 template <typename T>
 struct RBArgs {
     int n;
@@ -76,13 +86,118 @@ struct RBArgs {
     unsigned int* counter;
     double* result;
     const int* skip;
+    const T* e2;
+    const LevelScalars* esc;
+    int elevel;
+    T* y3;
+    const LevelScalars* rsc;
+    LevelScalars* ksc;
+    int klevel, kinner;
+    int* skip_rw;
+    LevelScalars* wsc;   // second SpMV of a K-cycle step: w1, w2 from its three dots
+    OuterScalars* aosc;  // the outer SpMV: alpha from (p, A p) and (p, r)
 };
+
+// Scalars of the fused modes, read once per thread at kernel start.
+template <typename T>
+struct KScal {
+    T a1, w1, w2;
+    bool two;
+};
+template <typename T, int MODE>
+__device__ __forceinline__ KScal<T> kscal(const RBArgs<T>& a) {
+    KScal<T> k{T(0), T(0), T(0), false};
+    if constexpr (MODE == RB_PRE1_RT) k.a1 = (T)a.rsc->a1;
+    if constexpr (MODE == RB_PROSMOOTH_E) {
+        const double w2 = a.esc->w2;
+        k.w1 = (T)a.esc->w1;
+        k.w2 = (T)w2;
+        k.two = w2 != 0.0;
+    }
+    return k;
+}
+// rho~_j = rho_j - a1 v1_j and e_I = w1 c1_I (+ w2 c2_I), as the unfused steps compute them.
+template <typename T>
+__device__ __forceinline__ T kc_rt_at(const RBArgs<T>& a, const KScal<T>& k, int j) {
+    return sub_rn(a.r[j], mul_rn(k.a1, a.d1[j]));
+}
+template <typename T>
+__device__ __forceinline__ T kc_e_at(const RBArgs<T>& a, const KScal<T>& k, int I) {
+    T v = mul_rn(k.w1, a.e[I]);
+    if (k.two) v = add_rn(v, mul_rn(k.w2, a.e2[I]));
+    return v;
+}
+
 // The vector entry a row-block kernel multiplies with column j in each mode.
 template <typename T, int MODE>
-__device__ __forceinline__ T rb_gather(const RBArgs<T>& a, int j) {
+__device__ __forceinline__ T rb_gather(const RBArgs<T>& a, const KScal<T>& k, int j) {
     if constexpr (MODE == RB_PRE1) return mul_rn(a.minv[j], a.r[j]);
+    else if constexpr (MODE == RB_PRE1_RT) return mul_rn(a.minv[j], kc_rt_at(a, k, j));
     else if constexpr (MODE == RB_PROSMOOTH) return add_rn(a.x[j], a.e[a.agg[j]]);
+    else if constexpr (MODE == RB_PROSMOOTH_E) return add_rn(a.x[j], kc_e_at(a, k, a.agg[j]));
     else return a.x[j];
+}
+
+// Kernel entry: false when the kernel lies inside a skipped second K-cycle step.  A fused
+// prolongation of level elevel-1 runs when the skip value is its own child's (elevel + 1),
+// which means the child skipped its second step, and clears it (block 0; a block that reads
+// the cleared value runs as well).
+template <typename T, int MODE>
+__device__ __forceinline__ bool rb_enter(const RBArgs<T>& a) {
+    if (!a.skip) return true;
+    const int sk = *(volatile const int*)a.skip;
+    if constexpr (MODE == RB_PROSMOOTH_E) {
+        if (sk != 0 && sk != a.elevel + 1) return false;
+        if (sk != 0 && blockIdx.x == 0 && threadIdx.x == 0) *a.skip_rw = 0;
+        return true;
+    } else {
+        return sk == 0;
+    }
+}
+
+// After the last block has summed rho1 = result[0] of a K-cycle's first SpMV: the second
+// step is skipped when rho1 <= 0 or the level takes one step (Section 4.3 guards).
+// It also sets a1 and the one-step weights (w1 = a1, w2 = 0), which a second step replaces.
+template <typename T>
+__device__ __forceinline__ void rb_kc_decide(const RBArgs<T>& a) {
+    const double rho1 = a.result[0], alpha1 = a.result[1];
+    const int skip2 = (!(rho1 > 0.0) || a.kinner < 2) ? 1 : 0;
+    const double a1 = rho1 > 0.0 ? alpha1 / rho1 : 0.0;
+    a.ksc->a1 = a1;
+    a.ksc->w1 = a1;
+    a.ksc->w2 = 0.0;
+    a.ksc->skip2 = skip2;
+    if (skip2 && a.kinner >= 2) *a.skip_rw = a.klevel + 1;
+}
+
+// After the last block has summed beta, gamma, alpha2 of a K-cycle's second step:
+// rho2 = beta - gamma^2 / rho1; when rho2 > 0, w1 = a1 - gamma alpha2 / (rho1 rho2) and
+// w2 = alpha2 / rho2 (Section 4.3 guards), else the one-step weights stand.
+template <typename T>
+__device__ __forceinline__ void rb_kc_weights(const RBArgs<T>& a) {
+    LevelScalars* sc = a.wsc;
+    const double rho1 = sc->rho1;
+    const double beta = a.result[0], gamma = a.result[1], alpha2 = a.result[2];
+    const double rho2 = beta - gamma * gamma / rho1;
+    if (rho1 > 0.0 && rho2 > 0.0) {
+        sc->w1 = sc->a1 - gamma * alpha2 / (rho1 * rho2);
+        sc->w2 = alpha2 / rho2;
+    }
+}
+
+// After the last block has summed (p, A p) and (p, r) of the outer iteration.
+template <typename T>
+__device__ __forceinline__ void rb_outer_alpha(const RBArgs<T>& a) {
+    const double pq = a.result[0], pr = a.result[1];
+    a.aosc->alpha_cur = pq > 0.0 ? pr / pq : 0.0;
+}
+
+// The hooks a row-block kernel runs in thread 0 of its last block.
+template <typename T>
+__device__ __forceinline__ void rb_last_block(const RBArgs<T>& a) {
+    if (a.ksc) rb_kc_decide(a);
+    if (a.wsc) rb_kc_weights(a);
+    if (a.aosc) rb_outer_alpha(a);
 }
 
 template <typename T>
@@ -158,6 +273,7 @@ template <typename T>
 int launch_outer_zq(Handle* h, int n, const T* z, const double* q, OuterScalars* osc);
 template <typename T>
 int launch_outer_p(Handle* h, int n, const T* z, double* p, OuterScalars* osc);
+int launch_outer_loop(Handle* h, cudaGraphConditionalHandle cond);
 int launch_outer_xr(Handle* h, int n, double* x, double* r, const double* p, const double* q,
                     OuterScalars* osc);
 int launch_dot(Handle* h, int n, const double* a, const double* b, double* result);

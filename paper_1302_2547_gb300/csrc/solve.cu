@@ -5,6 +5,8 @@
 // CUDA graph and replayed.
 #include <math.h>
 
+#include <cstddef>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -70,12 +72,27 @@ static RBArgs<T> rb_args(Handle* h, const Level& L) {
 }
 
 template <typename T>
-static int apply_K(Handle* h, int m, const T* in, T* out);
+static int apply_K(Handle* h, int m, const T* in, T* out, bool defer);
+
+// B_m's right-hand side rho~ = rho - (alpha1/rho1) v1 of level m's own K-cycle, formed by
+// B_m's first sweep (RB_PRE1_RT), which also stores it in B_m's `in` for the later steps.
+template <typename T>
+struct RtFuse {
+    const T* rho;
+    const T* v1;
+    const LevelScalars* sc;
+};
+
+// Whether K_m may leave e = w1 c1 + w2 c2 unwritten for the caller's prolongation to form
+// (RB_PROSMOOTH_E): not on the coarsest level (exact solve) or a fused tail level.
+static bool can_defer(const Handle* h, int m) {
+    return m < h->nlev - 1 && !(h->tail_level > 0 && m == h->tail_level);
+}
 
 // out = B_l(in): `pre` l1-Jacobi sweeps from zero, residual restriction, coarse correction
 // by K_{l+1}, prolongation, `post` sweeps.  On the coarsest level, the exact solve.
 template <typename T>
-static int apply_B(Handle* h, int l, const T* in, T* out) {
+static int apply_B(Handle* h, int l, const T* in, T* out, const RtFuse<T>* rf = nullptr) {
     const int* skip = &h->ctrl->skip;
     if (l == h->nlev - 1) return launch_dense_apply<T>(h, h->nco, h->coarse_inv, in, out, skip);
     Level& L = h->lev[l];
@@ -96,8 +113,16 @@ static int apply_B(Handle* h, int l, const T* in, T* out) {
         T* y = buf(k++);
         a.y = y;
         a.y2 = s;
+        int mode = RB_PRE1;
+        if (rf) {  // r = rho~ formed here and stored in `in`
+            mode = RB_PRE1_RT;
+            a.r = rf->rho;
+            a.d1 = rf->v1;
+            a.rsc = rf->sc;
+            a.y3 = const_cast<T*>(in);
+        }
         int ps = prof_begin(h, UAAMG_KCLASS_SMOOTH0, l);
-        if ((st = launch_rowblock<T>(h, RB_PRE1, 0, a))) return st;
+        if ((st = launch_rowblock<T>(h, mode, 0, a))) return st;
         prof_end(h, ps);
         x = y;
         for (int i = 1; i < pre; i++) {
@@ -122,7 +147,8 @@ static int apply_B(Handle* h, int l, const T* in, T* out) {
         if ((st = launch_copy<T>(h, L.n, nullptr, s, skip))) return st;  // x = 0
         x = s;
     }
-    if ((st = apply_K<T>(h, l + 1, rc, ec))) return st;
+    const bool defer = post >= 1 && can_defer(h, l + 1);
+    if ((st = apply_K<T>(h, l + 1, rc, ec, defer))) return st;
     {
         RBArgs<T> a = rb_args<T>(h, L);
         a.r = in;
@@ -131,7 +157,14 @@ static int apply_B(Handle* h, int l, const T* in, T* out) {
         a.e = ec;
         T* y = buf(k++);
         a.y = y;
-        if (post >= 1) {
+        if (defer) {  // e = w1 c1 + w2 c2 of level l+1 formed in the gather
+            a.e = (const T*)C.c1;
+            a.e2 = (const T*)C.c2;
+            a.esc = C.sc;
+            a.elevel = l + 1;
+            a.skip_rw = &h->ctrl->skip;
+            if ((st = launch_rowblock<T>(h, RB_PROSMOOTH_E, 0, a))) return st;
+        } else if (post >= 1) {
             if ((st = launch_rowblock<T>(h, RB_PROSMOOTH, 0, a))) return st;
         } else {
             if ((st = launch_prolong<T>(h, L.n, x, L.agg, ec, y, skip))) return st;
@@ -151,9 +184,10 @@ static int apply_B(Handle* h, int l, const T* in, T* out) {
 }
 
 // out = K_m(in) for m >= 1: two flexible-CG steps on A_m e = in preconditioned by B_m
-// (exact solve on the coarsest level).
+// (exact solve on the coarsest level).  With `defer`, out is not written: the caller's
+// prolongation forms e from c1, c2 and the level's scalars.
 template <typename T>
-static int apply_K(Handle* h, int m, const T* in, T* out) {
+static int apply_K(Handle* h, int m, const T* in, T* out, bool defer) {
     const int* skip = &h->ctrl->skip;
     if (m == h->nlev - 1) return launch_dense_apply<T>(h, h->nco, h->coarse_inv, in, out, skip);
     if (h->tail_level > 0 && m == h->tail_level && in == (const T*)h->lev[m].rhs &&
@@ -162,6 +196,10 @@ static int apply_K(Handle* h, int m, const T* in, T* out) {
     Level& L = h->lev[m];
     T *c1 = (T*)L.c1, *v1 = (T*)L.v1, *rt = (T*)L.rt, *c2 = (T*)L.c2, *v2 = (T*)L.v2;
     int st;
+    int inner = h->p.kcycle_inner;
+    if (inner == 2 && h->p.kcycle_ratio > 0.0 &&
+        (double)h->lev[m - 1].n < h->p.kcycle_ratio * (double)L.n)
+        inner = 1;  // level reached by weak coarsening: one step
     if ((st = apply_B<T>(h, m, in, c1))) return st;
     {
         RBArgs<T> a = rb_args<T>(h, L);
@@ -169,30 +207,39 @@ static int apply_K(Handle* h, int m, const T* in, T* out) {
         a.y = v1;
         a.d1 = in;
         a.result = &L.sc->rho1;  // (c1, A c1), (c1, rho)
+        a.ksc = L.sc;            // then: second step or not
+        a.klevel = m;
+        a.kinner = inner;
+        a.skip_rw = &h->ctrl->skip;
         if ((st = launch_rowblock<T>(h, RB_SPMV, 2, a))) return st;
     }
-    int inner = h->p.kcycle_inner;
-    if (inner == 2 && h->p.kcycle_ratio > 0.0 &&
-        (double)h->lev[m - 1].n < h->p.kcycle_ratio * (double)L.n)
-        inner = 1;  // level reached by weak coarsening: one step
-    if ((st = launch_kc_rt<T>(h, m, L.n, in, v1, rt, L.sc, inner, h->p.kcycle_tau, h->ctrl)))
+    // rho~ is formed by the second B_m's first sweep, unless the tau test needs its norm
+    // first or B_m has no pre-sweep
+    const bool tau = h->p.kcycle_tau > 0.0 && inner >= 2;
+    const bool fuse_rt = inner >= 2 && !tau && h->p.pre >= 1;
+    if (inner >= 2 && !fuse_rt &&
+        (st = launch_kc_rt<T>(h, m, L.n, in, v1, rt, L.sc, inner, h->p.kcycle_tau, h->ctrl)))
         return st;
     if (inner >= 2) {
-        if ((st = apply_B<T>(h, m, rt, c2))) return st;
+        const RtFuse<T> rf{in, v1, L.sc};
+        if ((st = apply_B<T>(h, m, rt, c2, fuse_rt ? &rf : nullptr))) return st;
         RBArgs<T> a = rb_args<T>(h, L);
         a.x = c2;
         a.y = v2;
         a.d1 = v1;
         a.d2 = rt;
         a.result = &L.sc->beta;  // (c2, A c2), (c2, v1), (c2, rho~)
+        a.wsc = L.sc;            // then w1, w2
         if ((st = launch_rowblock<T>(h, RB_SPMV, 3, a))) return st;
     }
+    if (defer) return UAAMG_OK;
     return launch_kc_combine<T>(h, m, L.n, c1, c2, out, L.sc, h->ctrl);
 }
 
-// One outer flexible-CG iteration (everything on the device).
+// One outer flexible-CG iteration (everything on the device).  to_host: copy the outer
+// scalars to the pinned mirror at the end.
 template <typename T>
-static int outer_iteration(Handle* h) {
+static int outer_iteration(Handle* h, bool to_host) {
     Level& L0 = h->lev[0];
     const int n = L0.n;
     int st;
@@ -220,17 +267,95 @@ static int outer_iteration(Handle* h) {
         a.partials = h->partials;
         a.counter = &h->ctrl->red_count;
         a.result = &h->osc->pq;  // (p, A p), (p, r)
+        a.aosc = h->osc;         // then alpha
         int ps = prof_begin(h, UAAMG_KCLASS_SPMV64, 0);
         if ((st = launch_rowblock<double>(h, RB_SPMV, 2, a))) return st;
         prof_end(h, ps);
     }
     if ((st = launch_outer_xr(h, n, h->x, h->r, h->p_, h->q, h->osc))) return st;
-    return launch_to_host_scalars(h);
+    return to_host ? launch_to_host_scalars(h) : UAAMG_OK;
 }
 
-static int run_iteration(Handle* h) {
-    if (h->p.precision == UAAMG_MIXED) return outer_iteration<float>(h);
-    return outer_iteration<double>(h);
+static int run_iteration(Handle* h, bool to_host = true) {
+    if (h->p.precision == UAAMG_MIXED) return outer_iteration<float>(h, to_host);
+    return outer_iteration<double>(h, to_host);
+}
+
+// The whole iteration loop as one graph: a while node whose body is one iteration followed
+// by k_outer_loop, which sets the node's condition on the device.  One launch runs every
+// iteration with no host round trip in between.  (Event nodes cannot sit in a conditional
+// body, so kernel-class profiling keeps the graph of one iteration.)
+static int ensure_loop_graph(Handle* h) {
+    if (h->loop_graph) return UAAMG_OK;
+    int st = UAAMG_OK;
+    if (!h->d_hist) {
+        h->hist_cap = h->p.max_iter + 2;
+        h->d_hist = dalloc<double>(h, (size_t)h->hist_cap, &st);
+        if (st) return st;
+    }
+    cudaGraph_t g = nullptr;
+    if ((st = check_cuda(cudaGraphCreate(&g, 0)))) return st;
+    cudaGraphConditionalHandle cond;
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t node;
+    st = check_cuda(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+    if (st == UAAMG_OK) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        st = check_cuda(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    }
+    if (st == UAAMG_OK) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        h->capturing = true;
+        const long long nodes0 = h->graph_nodes;
+        h->graph_nodes = 0;
+        st = check_cuda(cudaStreamBeginCaptureToGraph(h->work, body, nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeThreadLocal));
+        if (st == UAAMG_OK) {
+            int st2 = run_iteration(h, false);
+            if (st2 == UAAMG_OK) st2 = launch_outer_loop(h, cond);
+            st = check_cuda(cudaStreamEndCapture(h->work, &body));
+            if (st2) st = st2;
+        }
+        h->loop_nodes = h->graph_nodes;
+        h->graph_nodes = nodes0;
+        h->capturing = false;
+    }
+    if (st == UAAMG_OK) st = check_cuda(cudaGraphInstantiate(&h->loop_graph, g, 0));
+    cudaGraphDestroy(g);
+    if (st != UAAMG_OK) {
+        h->loop_graph = nullptr;
+        cudaGetLastError();
+    }
+    return st;
+}
+
+// Runs up to `limit` iterations on the device until rr <= stop_rr or breakdown; returns the
+// iterations done in *done and appends their relative residuals to the history.
+static int iterate_loop(Handle* h, double stop_rr, int limit, int* done) {
+    OuterScalars* o = h->osc_host;
+    o->stop_rr = stop_rr;
+    o->it = 0;
+    o->it_limit = limit;
+    int st = check_cuda(cudaMemcpyAsync(&h->osc->stop_rr, &o->stop_rr,
+                                        offsetof(OuterScalars, it_limit) + sizeof(int) -
+                                            offsetof(OuterScalars, stop_rr),
+                                        cudaMemcpyHostToDevice, h->work));
+    if (st == UAAMG_OK) st = check_cuda(cudaGraphLaunch(h->loop_graph, h->work));
+    if (st == UAAMG_OK) st = launch_to_host_scalars(h);
+    if (st == UAAMG_OK) st = check_cuda(cudaStreamSynchronize(h->work));
+    if (st) return st;
+    *done = o->it;
+    count_launch(h, h->loop_nodes * o->it);
+    std::vector<double> rel(o->it + 1);
+    if (o->it > 0) {
+        st = check_cuda(cudaMemcpy(rel.data(), h->d_hist + 1, sizeof(double) * o->it,
+                                   cudaMemcpyDeviceToHost));
+        for (int i = 0; i < o->it; i++) h->hist.push_back(rel[i]);
+    }
+    return st;
 }
 
 static int ensure_graph(Handle* h) {
@@ -351,9 +476,26 @@ int solve(Handle* h, const double* b, double* x, double tol, int use_guess, int*
     }
     h->hist.push_back(rn / bn);
     if (rn <= tol * bn) status = UAAMG_OK;
-    if (status != UAAMG_OK && (st = ensure_graph(h))) return st;
     int k = 0;
-    while (status != UAAMG_OK && k < h->p.max_iter) {
+    const bool loop = h->p.use_graphs && !h->prof_class && h->osc_host->bb > 0.0;
+    if (status != UAAMG_OK && loop && (st = ensure_loop_graph(h))) return st;
+    while (loop && status != UAAMG_OK && k < h->p.max_iter) {
+        // iterate on the device until the recursive residual passes, then confirm it
+        int done = 0;
+        const double stop_rr = (tol * bn) * (tol * bn);
+        if ((st = iterate_loop(h, stop_rr, h->p.max_iter - k, &done))) return st;
+        k += done;
+        if (h->osc_host->breakdown || done == 0) break;
+        rn = sqrt(h->osc_host->rr);
+        if (rn <= tol * bn) {
+            if ((st = true_residual(h))) return st;
+            rn = sqrt(h->osc_host->rr);
+            h->hist.back() = rn / bn;
+            if (rn <= tol * bn) status = UAAMG_OK;
+        }
+    }
+    if (!loop && status != UAAMG_OK && (st = ensure_graph(h))) return st;
+    while (!loop && status != UAAMG_OK && k < h->p.max_iter) {
         if ((st = iterate_once(h))) return st;
         k++;
         if (h->osc_host->breakdown) break;
@@ -398,7 +540,7 @@ static int apply_host(Handle* h, int which, int l, const double* in, double* out
     }
     (void)tmp_in;
     if (which == 0) st = apply_B<T>(h, l, tin, tout);
-    else st = apply_K<T>(h, l, tin, tout);
+    else st = apply_K<T>(h, l, tin, tout, false);
     if (st == UAAMG_OK) {
         std::vector<T> host(n);
         cudaMemcpyAsync(host.data(), tout, sizeof(T) * n, cudaMemcpyDeviceToHost, h->work);
