@@ -7,8 +7,8 @@
  *
  *   setup (Algorithm 1, setup phase): per level, priorities (Eq. 3.2), parallel aggregation
  *     passes (Algorithm 2), coarse numbering by ascending root (Section 5.1), coarse
- *     operator by aggregate sums (Eq. 2.4), l1-Jacobi data (Section 4.1), and a dense
- *     Cholesky-based inverse of the coarsest matrix.
+ *     operator by aggregate sums (Eq. 2.4), l1-Jacobi data (Section 4.1), and the dense
+ *     FP64 inverse of the coarsest matrix (symmetric Gauss-Jordan sweep).
  *   solve (Algorithm 1, solve phase, with the K-cycle of Section 4.3 as preconditioner of
  *     a flexible conjugate gradient, Sections 1 and 4.4): l1-Jacobi smoothing fused into
  *     CSR SpMV, aggregate-sum restriction and piecewise-constant prolongation
@@ -244,7 +244,7 @@ void uaamg_server_destroy(uaamg_server* s);
  * agg[i] = the coarse vertex of fine vertex i (device int32[n], caller-owned) and *nc (host)
  * = the number of aggregates.  A is validated like in uaamg_setup and must be on the device
  * (A->on_device = 1).  Nothing is allocated: all scratch lives in one static device array
- * of about 12 MB that every GPU loading this library holds until the process exits, so
+ * of about 19 MB that every GPU loading this library holds until the process exits, so
  * A->n may be at most 262,144 (larger graphs return UAAMG_ERR_UNSUPPORTED before any device
  * work).  The first call on a device looks up that array's address (cudaGetSymbolAddress)
  * and should therefore come before any stream capture.  Every call shares the array and

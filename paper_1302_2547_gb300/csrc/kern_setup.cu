@@ -1020,9 +1020,9 @@ int launch_level_finish(Handle* h, int n, long long nnz, const int* rowptr, cons
 }
 
 // ---------------------------------------------------------------------------------------
-// Coarsest level, Algorithm 1 "solve exactly": dense Cholesky factor L L^T of the coarsest
-// matrix (one block), then its inverse by one forward and one backward substitution per
-// column, so that each coarsest solve of the cycle is a dense matrix-vector product.
+// Coarsest level, Algorithm 1 "solve exactly": the explicit FP64 inverse of the coarsest
+// matrix (k_gj_inverse below), so that each coarsest solve of the cycle is a dense
+// matrix-vector product.
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads)
 k_dense_gather(int n, const int* __restrict__ rowptr, const int* __restrict__ col,

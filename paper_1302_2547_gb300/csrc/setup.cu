@@ -242,7 +242,7 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
                                       L.val32)))
             goto done;
     }
-    {  // coarsest level: dense inverse through the Cholesky factor
+    {  // coarsest level: its dense FP64 inverse
         Level& Lc = h->lev[h->nlev - 1];
         h->nco = Lc.n;
         if (Lc.n > kMaxCoarsest) {
