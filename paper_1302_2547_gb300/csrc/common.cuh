@@ -52,6 +52,7 @@ struct LevelScalars {
     // FP64 divisions would make the element-wise kernels FP64-bound):
     //   a1 = alpha1 / rho1 (0 when rho1 <= 0); e = w1 c1 + w2 c2
     double a1, w1, w2;
+    float a1f, w1f, w2f, pad2;  // the same, rounded once for FP32 cycles
 };
 
 // FP64 scalars of the outer flexible CG.

@@ -1,26 +1,26 @@
 // kern_tma.cu -- the row-block SpMV kernels of the large levels with their matrix stream
-// staged by the Tensor Memory Accelerator.
+// staged by the Tensor Memory Accelerator, one pipeline per warp.
 //
-// A persistent block walks row blocks rb = blockIdx.x, blockIdx.x + G, ...  The entries of
-// a row block are one contiguous range of col/val; thread 0 copies the ranges of the next
-// two row blocks into a two-stage shared-memory ring with 1D bulk copies
-// (cp.async.bulk ... mbarrier::complete_tx), so the HBM stream of the matrix runs ahead
-// of the computation instead of sitting on each block's critical path.  Each thread then
-// walks its own row in the staged arrays, gathering the vector entries eight at a time,
-// adds the row in stored order with fused multiply-adds and applies the same fused epilogue
-// as k_rowblock: every vector entry is bit-identical to that kernel's with one thread per
-// row (the fused inner products are summed in another fixed order, as each block covers
-// several row blocks).  A row block whose entries do not fit a stage is read directly from
-// global memory.  Every wait on a stage barrier is bounded; on timeout the block records
-// kErrTimeout, waits (bounded) for its copies in flight and leaves.
+// A persistent grid; every warp walks its own chunks of 32 rows, c = w, w + W, ... (W warps
+// in the grid).  The entries of a chunk are one contiguous range of col/val.  Lane 0 of the
+// warp copies the ranges of the warp's next two chunks into the warp's own two-stage
+// shared-memory ring with 1D bulk copies (cp.async.bulk ... mbarrier::complete_tx), so the
+// HBM stream of the matrix runs ahead of the computation.  Each lane then walks its own row
+// in the staged arrays, gathering the vector entries eight at a time, adds the row in stored
+// order with fused multiply-adds and applies the same fused epilogue as k_rowblock: every
+// vector entry is bit-identical to that kernel's with one thread per row (the fused inner
+// products are summed in another fixed order).  Warps never wait for each other, so no
+// block-wide barrier sits between a chunk's gathers and the next one's.  A chunk whose
+// entries do not fit a stage is read directly from global memory.  Every wait on a stage
+// is bounded; on timeout the warp records kErrTimeout, waits (bounded) for its copies in
+// flight, stops its work and still joins the block's final reduction.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace uaamg {
 
-constexpr int kTmaRows = 256;
-constexpr int kTmaCap = 2048;              // entries per stage (16-byte aligned range)
-constexpr int kTmaBatch = 8;               // gathers a thread has in flight per row
+constexpr int kTmaWarps = kThreads / 32;   // warps per block, each with its own pipeline
+constexpr int kTmaBatch = 8;               // gathers a lane has in flight per row
 constexpr long long kTmaSpin = 1LL << 31;  // clock cycles before a stage wait gives up
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -54,24 +54,25 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 
-template <typename T>
-struct TmaSmem {
-    int col[2][kTmaCap];
-    T val[2][kTmaCap];
+// One warp's two stages of CAP entries each.
+template <typename T, int CAP>
+struct WarpStages {
+    int col[2][CAP];
+    T val[2][CAP];
     uint64_t bar[2];
 };
 
-// Issues the copies of the entry range [k0, k1) into stage s; false when it does not fit.
-template <typename T>
-__device__ __forceinline__ bool tma_issue(const RBArgs<T>& a, TmaSmem<T>& sm, int k0, int k1,
-                                          int s) {
+// Lane 0: copies of the entry range [k0, k1) into stage s; false when it does not fit.
+template <typename T, int CAP>
+__device__ __forceinline__ bool tma_issue(const RBArgs<T>& a, WarpStages<T, CAP>& ws, int k0,
+                                          int k1, int s) {
     const int a0 = k0 & ~3, a1 = (k1 + 3) & ~3;
     const int cnt = a1 - a0;
-    if (cnt > kTmaCap || cnt <= 0) return false;
+    if (cnt > CAP || cnt <= 0) return false;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(&sm.bar[s], (unsigned)cnt * (4u + (unsigned)sizeof(T)));
-    bulk_g2s(sm.col[s], a.col + a0, (unsigned)cnt * 4u, &sm.bar[s]);
-    bulk_g2s(sm.val[s], a.val + a0, (unsigned)cnt * (unsigned)sizeof(T), &sm.bar[s]);
+    mbar_arrive_expect_tx(&ws.bar[s], (unsigned)cnt * (4u + (unsigned)sizeof(T)));
+    bulk_g2s(ws.col[s], a.col + a0, (unsigned)cnt * 4u, &ws.bar[s]);
+    bulk_g2s(ws.val[s], a.val + a0, (unsigned)cnt * (unsigned)sizeof(T), &ws.bar[s]);
     return true;
 }
 
@@ -96,46 +97,46 @@ __device__ __forceinline__ T row_sum(const RBArgs<T>& a, const KScal<T>& ks, con
     return acc;
 }
 
-template <typename T, int MODE, int ND>
-__global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ctrl) {
+template <typename T, int MODE, int ND, int CAP>
+__global__ void __launch_bounds__(kThreads) k_rowwarp_tma(RBArgs<T> a, Ctrl* ctrl) {
     if (!rb_enter<T, MODE>(a)) return;
     const KScal<T> ks = kscal<T, MODE>(a);
     extern __shared__ __align__(128) unsigned char dyn[];
-    TmaSmem<T>& sm = *reinterpret_cast<TmaSmem<T>*>(dyn);
-    __shared__ int staged[2];  // 1 when the stage holds its row block's entries
-    const int nblk = (a.n + kTmaRows - 1) / kTmaRows;
-    const int G = gridDim.x;
-    if (threadIdx.x == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpStages<T, CAP>& ws = reinterpret_cast<WarpStages<T, CAP>*>(dyn)[warp];
+    const int nch = (a.n + 31) >> 5;
+    const int W = gridDim.x * kTmaWarps;
+    const int gw = blockIdx.x * kTmaWarps + warp;
+    unsigned staged = 0;  // bit s: stage s holds its chunk (lane 0's copy, broadcast)
+    if (lane == 0) {
+        mbar_init(&ws.bar[0], 1);
+        mbar_init(&ws.bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int s = 0; s < 2; s++) {
-            const int rb = blockIdx.x + s * G;
-            staged[s] = 0;
-            if (rb < nblk)
-                staged[s] = tma_issue<T>(a, sm, a.rowptr[rb * kTmaRows],
-                                         a.rowptr[min(a.n, (rb + 1) * kTmaRows)], s) ? 1 : 0;
+            const int c = gw + s * W;
+            if (c < nch && tma_issue<T, CAP>(a, ws, a.rowptr[c << 5],
+                                             a.rowptr[min(a.n, (c + 1) << 5)], s))
+                staged |= 1u << s;
         }
     }
-    __syncthreads();
+    staged = __shfl_sync(0xffffffffu, staged, 0);
+    __syncwarp();
     unsigned phase = 0u;  // bit s: parity of the next completion of stage s
     double dv[ND > 0 ? ND : 1];
 #pragma unroll
     for (int k = 0; k < (ND > 0 ? ND : 1); k++) dv[k] = 0.0;
-    bool failed = false;
     for (int it = 0;; it++) {
-        const int rb = blockIdx.x + it * G;
-        if (rb >= nblk) break;
+        const int c = gw + it * W;
+        if (c >= nch) break;
         const int s = it & 1;
-        const int r0 = rb * kTmaRows, r1 = min(a.n, r0 + kTmaRows);
-        const int row = r0 + threadIdx.x;
-        // thread 0 loads the bounds of the row block it copies into this stage next, so the
-        // copy is issued without a memory round trip on the block's path
-        const int nrb = rb + 2 * G;
+        const int r0 = c << 5, r1 = min(a.n, r0 + 32);
+        const int row = r0 + lane;
+        // lane 0 loads the bounds of the chunk it copies into this stage next
+        const int nc = c + 2 * W;
         int nk0 = 0, nk1 = 0;
-        if (threadIdx.x == 0 && nrb < nblk) {
-            nk0 = a.rowptr[nrb * kTmaRows];
-            nk1 = a.rowptr[min(a.n, (nrb + 1) * kTmaRows)];
+        if (lane == 0 && nc < nch) {
+            nk0 = a.rowptr[nc << 5];
+            nk1 = a.rowptr[min(a.n, (nc + 1) << 5)];
         }
         int rs = 0, re = 0;
         T ri = T(0), mi = T(0), xi = T(0);
@@ -152,33 +153,35 @@ __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ct
             if constexpr (MODE == RB_SMOOTH || pro || MODE == RB_SPMV) xi = a.x[row];
             if constexpr (pro) gi = a.agg[row];
         }
+        const int k0 = __shfl_sync(0xffffffffu, rs, 0);  // lane 0 holds row r0
         T acc = T(0);
-        if (staged[s]) {
-            const int a0 = a.rowptr[r0] & ~3;
-            long long t0 = clock64();
-            while (!mbar_try_wait(&sm.bar[s], (phase >> s) & 1u)) {
+        if ((staged >> s) & 1u) {
+            bool failed = false;
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&ws.bar[s], (phase >> s) & 1u)) {
                 if (clock64() - t0 > kTmaSpin) {
                     failed = true;
                     break;
                 }
             }
-            if (__syncthreads_or(failed)) {  // one decision for the whole block
-                if (threadIdx.x == 0) {
+            if (__any_sync(0xffffffffu, failed)) {
+                if (lane == 0) {
                     atomicOr(&ctrl->err, kErrTimeout);
-                    // let the copies still in flight land before the block releases its
-                    // shared memory, again with a bound
+                    // let the copies still in flight land before this warp stops using them
                     for (int q = 0; q < 2; q++) {
-                        if (!staged[q]) continue;
+                        if (!((staged >> q) & 1u)) continue;
                         const long long t1 = clock64();
-                        while (!mbar_try_wait(&sm.bar[q], (phase >> q) & 1u) &&
+                        while (!mbar_try_wait(&ws.bar[q], (phase >> q) & 1u) &&
                                clock64() - t1 < kTmaSpin) {
                         }
                     }
                 }
-                return;
+                __syncwarp();
+                break;  // no more work from this warp; it still joins the block reduction
             }
             phase ^= 1u << s;
-            if (row < r1) acc = row_sum<T, MODE>(a, ks, sm.col[s], sm.val[s], rs - a0, re - a0);
+            const int a0 = k0 & ~3;
+            if (row < r1) acc = row_sum<T, MODE>(a, ks, ws.col[s], ws.val[s], rs - a0, re - a0);
         } else if (row < r1) {  // entries beyond a stage: straight from global memory
             acc = row_sum<T, MODE>(a, ks, a.col, a.val, rs, re);
         }
@@ -211,40 +214,42 @@ __global__ void __launch_bounds__(kThreads) k_rowblock_tma(RBArgs<T> a, Ctrl* ct
                 if constexpr (ND >= 3) dv[2] = fma(xd, (double)a.d2[i], dv[2]);
             }
         }
-        // Stage s is free once every thread is past this barrier.  staged[s] is read next
-        // two iterations later, after at least one more barrier.
-        __syncthreads();
-        if (threadIdx.x == 0) staged[s] = (nrb < nblk) ? (tma_issue<T>(a, sm, nk0, nk1, s) ? 1 : 0) : 0;
+        __syncwarp();  // every lane is done with stage s
+        if (lane == 0) {
+            staged &= ~(1u << s);
+            if (nc < nch && tma_issue<T, CAP>(a, ws, nk0, nk1, s)) staged |= 1u << s;
+        }
+        staged = __shfl_sync(0xffffffffu, staged, 0);
     }
     if constexpr (ND > 0) {
         if (grid_reduce<ND>(dv, a.partials, a.counter, a.result)) rb_last_block(a);
     }
 }
 
-template <typename T, int MODE, int ND>
+template <typename T, int MODE, int ND, int CAP>
 static int launch_one(Handle* h, const RBArgs<T>& a) {
     static int grid_cache[64] = {0};
-    const size_t smem = sizeof(TmaSmem<T>);
-    int dev = h->device < 64 ? h->device : 0;
+    const size_t smem = sizeof(WarpStages<T, CAP>) * kTmaWarps;
+    const int dev = h->device < 64 ? h->device : 0;
     if (!grid_cache[dev]) {
-        cudaFuncSetAttribute(k_rowblock_tma<T, MODE, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        cudaFuncSetAttribute(k_rowwarp_tma<T, MODE, ND, CAP>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowblock_tma<T, MODE, ND>, kThreads,
-                                                      smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowwarp_tma<T, MODE, ND, CAP>,
+                                                      kThreads, smem);
         grid_cache[dev] = (per_sm > 0 ? per_sm : 1) * h->num_sms;
     }
-    const int nblk = grid_for(a.n, kTmaRows);
+    const int nblk = grid_for((a.n + 31) / 32, kTmaWarps);
     const int grid = nblk < grid_cache[dev] ? nblk : grid_cache[dev];
-    k_rowblock_tma<T, MODE, ND><<<grid, kThreads, smem, h->work>>>(a, h->ctrl);
+    k_rowwarp_tma<T, MODE, ND, CAP><<<grid, kThreads, smem, h->work>>>(a, h->ctrl);
     count_launch(h);
     return check_cuda(cudaGetLastError());
 }
 
-template <typename T>
-int launch_rowblock_tma(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
+template <typename T, int CAP>
+static int launch_cap(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
 #define TMA_CASE(M, D) \
-    if (mode == M && ndots == D) return launch_one<T, M, D>(h, a);
+    if (mode == M && ndots == D) return launch_one<T, M, D, CAP>(h, a);
     TMA_CASE(RB_PRE1, 0)
     TMA_CASE(RB_PRE1_RT, 0)
     TMA_CASE(RB_PROSMOOTH_E, 0)
@@ -257,6 +262,15 @@ int launch_rowblock_tma(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
     TMA_CASE(RB_SPMV, 3)
 #undef TMA_CASE
     return UAAMG_ERR_INVALID_ARG;
+}
+
+// Stage size from the average row length: a chunk of 32 rows of a 7-point stencil (224
+// entries plus up to 6 of alignment) fits 256 entries; longer rows take 512.
+template <typename T>
+int launch_rowblock_tma(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
+    const bool short_rows = a.n > 0 && a.nnz > 0 && a.nnz * 4 <= (long long)a.n * 29;
+    return short_rows ? launch_cap<T, 256>(h, mode, ndots, a)
+                      : launch_cap<T, 512>(h, mode, ndots, a);
 }
 template int launch_rowblock_tma<float>(Handle*, int, int, const RBArgs<float>&);
 template int launch_rowblock_tma<double>(Handle*, int, int, const RBArgs<double>&);

@@ -70,6 +70,7 @@ template <typename T>
 struct RBArgs {
     int n;
     int rows;  // rows per block: 256, 128, 64 or 32 (256 / rows threads share a row)
+    long long nnz;  // stored entries (0 if not given)
     const int* rowptr;
     const int* col;
     const T* val;
@@ -107,12 +108,20 @@ struct KScal {
 template <typename T, int MODE>
 __device__ __forceinline__ KScal<T> kscal(const RBArgs<T>& a) {
     KScal<T> k{T(0), T(0), T(0), false};
-    if constexpr (MODE == RB_PRE1_RT) k.a1 = (T)a.rsc->a1;
-    if constexpr (MODE == RB_PROSMOOTH_E) {
-        const double w2 = a.esc->w2;
-        k.w1 = (T)a.esc->w1;
-        k.w2 = (T)w2;
-        k.two = w2 != 0.0;
+    if constexpr (sizeof(T) == 4) {  // FP32 copies rounded once by the reduction hooks
+        if constexpr (MODE == RB_PRE1_RT) k.a1 = a.rsc->a1f;
+        if constexpr (MODE == RB_PROSMOOTH_E) {
+            k.w1 = a.esc->w1f;
+            k.w2 = a.esc->w2f;
+            k.two = a.esc->w2 != 0.0;
+        }
+    } else {
+        if constexpr (MODE == RB_PRE1_RT) k.a1 = a.rsc->a1;
+        if constexpr (MODE == RB_PROSMOOTH_E) {
+            k.w1 = a.esc->w1;
+            k.w2 = a.esc->w2;
+            k.two = a.esc->w2 != 0.0;
+        }
     }
     return k;
 }
@@ -166,6 +175,9 @@ __device__ __forceinline__ void rb_kc_decide(const RBArgs<T>& a) {
     a.ksc->a1 = a1;
     a.ksc->w1 = a1;
     a.ksc->w2 = 0.0;
+    a.ksc->a1f = (float)a1;
+    a.ksc->w1f = (float)a1;
+    a.ksc->w2f = 0.0f;
     a.ksc->skip2 = skip2;
     if (skip2 && a.kinner >= 2) *a.skip_rw = a.klevel + 1;
 }
@@ -182,6 +194,8 @@ __device__ __forceinline__ void rb_kc_weights(const RBArgs<T>& a) {
     if (rho1 > 0.0 && rho2 > 0.0) {
         sc->w1 = sc->a1 - gamma * alpha2 / (rho1 * rho2);
         sc->w2 = alpha2 / rho2;
+        sc->w1f = (float)sc->w1;
+        sc->w2f = (float)sc->w2;
     }
 }
 

@@ -60,6 +60,7 @@ template <typename T>
 static RBArgs<T> rb_args(Handle* h, const Level& L) {
     RBArgs<T> a{};
     a.n = L.n;
+    a.nnz = L.nnz;
     a.rows = L.rb_rows;
     a.rowptr = L.rowptr;
     a.col = L.col;
@@ -147,7 +148,10 @@ static int apply_B(Handle* h, int l, const T* in, T* out, const RtFuse<T>* rf = 
         if ((st = launch_copy<T>(h, L.n, nullptr, s, skip))) return st;  // x = 0
         x = s;
     }
-    const bool defer = post >= 1 && can_defer(h, l + 1);
+    // on a large level the fused form costs more in the sweep (registers, two gathers per
+    // coarse value) than one combine launch on the child saves
+    const bool defer = post >= 1 && can_defer(h, l + 1) &&
+                       !(h->p.tma_rows > 0 && L.n >= h->p.tma_rows);
     if ((st = apply_K<T>(h, l + 1, rc, ec, defer))) return st;
     {
         RBArgs<T> a = rb_args<T>(h, L);
@@ -257,6 +261,7 @@ static int outer_iteration(Handle* h, bool to_host) {
     {
         RBArgs<double> a{};
         a.n = n;
+        a.nnz = L0.nnz;
         a.rows = L0.rb_rows;
         a.rowptr = L0.rowptr;
         a.col = L0.col;
@@ -425,6 +430,7 @@ static int true_residual(Handle* h) {
     Level& L0 = h->lev[0];
     RBArgs<double> a{};
     a.n = L0.n;
+    a.nnz = L0.nnz;
     a.rows = L0.rb_rows;
     a.rowptr = L0.rowptr;
     a.col = L0.col;
@@ -526,11 +532,13 @@ static int apply_host(Handle* h, int which, int l, const double* in, double* out
     const int n = L.n;
     int st = UAAMG_OK;
     double* d = nullptr;
-    if ((st = check_cuda(cudaMalloc(&d, sizeof(double) * n * 2)))) return st;
+    // two vectors: the second starts 256-byte aligned and both carry tail padding, as the
+    // staged kernels copy 16-byte aligned, 16-byte rounded ranges
+    const size_t off = ((size_t)n + 31) & ~(size_t)31;
+    if ((st = check_cuda(cudaMalloc(&d, sizeof(double) * (2 * off + 8))))) return st;
     T* tin = (T*)L.rhs;
     T* tout = (T*)L.out;
-    T* tmp_in = nullptr;
-    if (l == 0 && sizeof(T) == 8) tin = (T*)(d + n);  // level-0 rhs aliases the outer residual
+    if (l == 0 && sizeof(T) == 8) tin = (T*)(d + off);  // level-0 rhs aliases the outer residual
     cudaMemcpyAsync(d, in, sizeof(double) * n, cudaMemcpyHostToDevice, h->work);
     cudaMemsetAsync(&h->ctrl->skip, 0, sizeof(int), h->work);
     if constexpr (sizeof(T) == 4) {
@@ -538,7 +546,6 @@ static int apply_host(Handle* h, int which, int l, const double* in, double* out
     } else {
         cudaMemcpyAsync(tin, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->work);
     }
-    (void)tmp_in;
     if (which == 0) st = apply_B<T>(h, l, tin, tout);
     else st = apply_K<T>(h, l, tin, tout, false);
     if (st == UAAMG_OK) {
