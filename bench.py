@@ -141,12 +141,15 @@ def workload():
 EAGER = False  # --eager: launch every kernel directly instead of replaying graphs
 TMA_ROWS = None  # --tma-rows: levels of at least this many rows use the TMA-staged kernels
 FUSE_BELOW = None  # --fuse-below: levels of at most this many rows run the one-block cycle
+SELL_ROWS = None  # --sell-rows: levels of at least this many rows use the sliced ELLPACK copy
 
 
 def bench_params(U, precision, profile_class=0):
     extra = {} if TMA_ROWS is None else {"tma_rows": TMA_ROWS}
     if FUSE_BELOW is not None:
         extra["fuse_below"] = FUSE_BELOW
+    if SELL_ROWS is not None:
+        extra["sell_rows"] = SELL_ROWS
     return U.uaamg_default_params(precision=precision, profile_class=profile_class,
                                   use_graphs=0 if EAGER else 1, **BENCH_PARAMS, **extra)
 
@@ -331,6 +334,7 @@ def run_gpu(args, rank, world):
                    **BENCH_PARAMS, "pass_mode": "single round (Algorithm 2)",
                    "tma_rows": bench_params(U, U.UAAMG_MIXED).tma_rows,
                    "fuse_below": bench_params(U, U.UAAMG_MIXED).fuse_below,
+                   "sell_rows": bench_params(U, U.UAAMG_MIXED).sell_rows,
                    "l2": "inputs larger than L2 (CSR 183 MB FP64 > 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "setup_ms": round(float(np.median([r[2]['setup_ms'] for r in rec])), 3),
@@ -388,11 +392,14 @@ def main():
                     help="row threshold of the TMA-staged row-block kernels (0 = off)")
     ap.add_argument("--fuse-below", type=int, default=None,
                     help="levels of at most this many rows run the one-block K-cycle (0 = off)")
+    ap.add_argument("--sell-rows", type=int, default=None,
+                    help="row threshold of the sliced ELLPACK level copies (0 = off)")
     args = ap.parse_args()
-    global EAGER, TMA_ROWS, FUSE_BELOW
+    global EAGER, TMA_ROWS, FUSE_BELOW, SELL_ROWS
     EAGER = args.eager
     TMA_ROWS = args.tma_rows
     FUSE_BELOW = args.fuse_below
+    SELL_ROWS = args.sell_rows
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
 

@@ -93,6 +93,11 @@ typedef struct uaamg_params {
                              with TMA bulk copies, one thread per row (0 = never); default
                              262144.  Changes no vector entry; fused inner products are summed
                              in another fixed order. */
+    int32_t sell_rows;    /* levels (except the coarsest) with at least this many rows also
+                             keep a sliced ELLPACK copy (slices of 32 rows, column-major;
+                             Section 4.4) that their row kernels read instead of the CSR;
+                             skipped where it would pad the entries by more than 25% or a row
+                             exceeds 65535 entries (0 = never).  Changes no vector entry. */
     int32_t fuse_below;   /* coarse levels with at most this many unknowns run their K-cycle
                              in one fused single-block kernel (pre = post = 1 only); 0 = off
                              (default: on GB300 one block is slower than launching) */

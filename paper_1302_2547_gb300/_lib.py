@@ -44,7 +44,7 @@ class uaamg_params(C.Structure):
                 ("use_graphs", C.c_int32), ("profile_class", C.c_int32),
                 ("agg_repeat", C.c_int32), ("kcycle_ratio", C.c_double),
                 ("min_coarsening", C.c_double), ("jacobi_omega", C.c_double),
-                ("tma_rows", C.c_int32), ("fuse_below", C.c_int32)]
+                ("tma_rows", C.c_int32), ("sell_rows", C.c_int32), ("fuse_below", C.c_int32)]
 
 
 class uaamg_stats(C.Structure):

@@ -77,7 +77,7 @@ static bool params_ok(const uaamg_params* p) {
            p->profile_class >= 0 && p->profile_class <= UAAMG_KCLASS_COARSE &&
            (p->agg_repeat == 1 || p->agg_repeat == 2) && p->kcycle_ratio >= 0.0 &&
            p->min_coarsening >= 0.0 && p->fuse_below >= 0 && p->jacobi_omega >= 0.0 &&
-           p->tma_rows >= 0;
+           p->tma_rows >= 0 && p->sell_rows >= 0;
 }
 
 }  // namespace uaamg
@@ -107,6 +107,7 @@ void uaamg_default_params(uaamg_params* p) {
     p->min_coarsening = 0.0;
     p->jacobi_omega = 0.0;
     p->tma_rows = 262144;
+    p->sell_rows = 0;
     p->fuse_below = 0;
 }
 

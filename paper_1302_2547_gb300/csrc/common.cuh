@@ -92,6 +92,14 @@ struct Level {
     int* members = nullptr;  // [n]
     int passes = 0;
     int rb_rows = kRowsPerBlock;  // rows per block of this level's row-block kernels
+    // sliced ELLPACK copy (levels with n >= sell_rows): slice offsets, row lengths, columns
+    // and values in slice layout; null when not built
+    int* sl_ptr = nullptr;
+    uint16_t* sl_len = nullptr;
+    int* sl_col = nullptr;
+    double* sl_val64 = nullptr;
+    float* sl_val32 = nullptr;
+    int sl_ns = 0;
     // K-cycle workspace in the handle's precision
     void *rhs = nullptr, *out = nullptr, *w = nullptr, *s = nullptr;
     void *c1 = nullptr, *v1 = nullptr, *rt = nullptr, *c2 = nullptr, *v2 = nullptr;

@@ -139,19 +139,11 @@ __global__ void __launch_bounds__(kThreads) k_rowwarp_tma(RBArgs<T> a, Ctrl* ctr
             nk1 = a.rowptr[min(a.n, (nc + 1) << 5)];
         }
         int rs = 0, re = 0;
-        T ri = T(0), mi = T(0), xi = T(0);
-        int gi = 0;
+        RowOps<T> o{};
         if (row < r1) {  // per-row operands, loaded before waiting on the stage
             rs = a.rowptr[row];
             re = a.rowptr[row + 1];
-            constexpr bool pro = MODE == RB_PROSMOOTH || MODE == RB_PROSMOOTH_E;
-            if constexpr (MODE == RB_PRE1_RT) ri = kc_rt_at(a, ks, row);
-            else if constexpr (MODE == RB_PRE1 || MODE == RB_SMOOTH || pro || MODE == RB_RESID)
-                ri = a.r[row];
-            if constexpr (MODE == RB_PRE1 || MODE == RB_PRE1_RT || MODE == RB_SMOOTH || pro)
-                mi = a.minv[row];
-            if constexpr (MODE == RB_SMOOTH || pro || MODE == RB_SPMV) xi = a.x[row];
-            if constexpr (pro) gi = a.agg[row];
+            o = rb_row_ops<T, MODE, ND>(a, ks, row);
         }
         const int k0 = __shfl_sync(0xffffffffu, rs, 0);  // lane 0 holds row r0
         T acc = T(0);
@@ -185,35 +177,7 @@ __global__ void __launch_bounds__(kThreads) k_rowwarp_tma(RBArgs<T> a, Ctrl* ctr
         } else if (row < r1) {  // entries beyond a stage: straight from global memory
             acc = row_sum<T, MODE>(a, ks, a.col, a.val, rs, re);
         }
-        if (row < r1) {
-            const int i = row;
-            if constexpr (MODE == RB_PRE1) {
-                a.y[i] = mul_rn(mi, ri);
-                a.y2[i] = sub_rn(ri, acc);
-            } else if constexpr (MODE == RB_PRE1_RT) {
-                a.y[i] = mul_rn(mi, ri);
-                a.y2[i] = sub_rn(ri, acc);
-                a.y3[i] = ri;
-            } else if constexpr (MODE == RB_SMOOTH) {
-                a.y[i] = add_rn(xi, mul_rn(mi, sub_rn(ri, acc)));
-            } else if constexpr (MODE == RB_RESID) {
-                const T yi = sub_rn(ri, acc);
-                a.y[i] = yi;
-                if constexpr (ND >= 1) dv[0] = fma((double)yi, (double)yi, dv[0]);
-            } else if constexpr (MODE == RB_PROSMOOTH) {
-                const T xp = add_rn(xi, a.e[gi]);
-                a.y[i] = add_rn(xp, mul_rn(mi, sub_rn(ri, acc)));
-            } else if constexpr (MODE == RB_PROSMOOTH_E) {
-                const T xp = add_rn(xi, kc_e_at(a, ks, gi));
-                a.y[i] = add_rn(xp, mul_rn(mi, sub_rn(ri, acc)));
-            } else {
-                a.y[i] = acc;
-                const double xd = (double)xi;
-                if constexpr (ND >= 1) dv[0] = fma(xd, (double)acc, dv[0]);
-                if constexpr (ND >= 2) dv[1] = fma(xd, (double)a.d1[i], dv[1]);
-                if constexpr (ND >= 3) dv[2] = fma(xd, (double)a.d2[i], dv[2]);
-            }
-        }
+        if (row < r1) rb_row_out<T, MODE, ND>(a, ks, row, acc, o, dv);
         __syncwarp();  // every lane is done with stage s
         if (lane == 0) {
             staged &= ~(1u << s);

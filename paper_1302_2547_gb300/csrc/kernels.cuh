@@ -97,6 +97,12 @@ struct RBArgs {
     int* skip_rw;
     LevelScalars* wsc;   // second SpMV of a K-cycle step: w1, w2 from its three dots
     OuterScalars* aosc;  // the outer SpMV: alpha from (p, A p) and (p, r)
+    // sliced ELLPACK copy of the level (sptr != null: the SELL kernels run)
+    const int* sptr;
+    const int* scol;
+    const T* sval;
+    const uint16_t* slen;
+    int nslices;
 };
 
 // Scalars of the fused modes, read once per thread at kernel start.
@@ -145,6 +151,59 @@ __device__ __forceinline__ T rb_gather(const RBArgs<T>& a, const KScal<T>& k, in
     else if constexpr (MODE == RB_PROSMOOTH) return add_rn(a.x[j], a.e[a.agg[j]]);
     else if constexpr (MODE == RB_PROSMOOTH_E) return add_rn(a.x[j], kc_e_at(a, k, a.agg[j]));
     else return a.x[j];
+}
+
+// The operands a one-thread-per-row kernel loads for row i before its sum, by mode.
+template <typename T>
+struct RowOps {
+    T ri, mi, xi, d1i, d2i;
+    int gi;
+};
+template <typename T, int MODE, int ND>
+__device__ __forceinline__ RowOps<T> rb_row_ops(const RBArgs<T>& a, const KScal<T>& ks, int i) {
+    RowOps<T> o{T(0), T(0), T(0), T(0), T(0), 0};
+    constexpr bool pro = MODE == RB_PROSMOOTH || MODE == RB_PROSMOOTH_E;
+    if constexpr (MODE == RB_PRE1_RT) o.ri = kc_rt_at(a, ks, i);
+    else if constexpr (MODE == RB_PRE1 || MODE == RB_SMOOTH || pro || MODE == RB_RESID)
+        o.ri = a.r[i];
+    if constexpr (MODE == RB_PRE1 || MODE == RB_PRE1_RT || MODE == RB_SMOOTH || pro)
+        o.mi = a.minv[i];
+    if constexpr (MODE == RB_SMOOTH || pro || MODE == RB_SPMV) o.xi = a.x[i];
+    if constexpr (MODE == RB_SPMV && ND >= 2) o.d1i = a.d1[i];
+    if constexpr (MODE == RB_SPMV && ND >= 3) o.d2i = a.d2[i];
+    if constexpr (pro) o.gi = a.agg[i];
+    return o;
+}
+// Row i's outputs from its sum acc = (A v)_i, by mode (the same arithmetic as k_rowblock).
+template <typename T, int MODE, int ND>
+__device__ __forceinline__ void rb_row_out(const RBArgs<T>& a, const KScal<T>& ks, int i, T acc,
+                                           const RowOps<T>& o, double (&dv)[ND > 0 ? ND : 1]) {
+    if constexpr (MODE == RB_PRE1) {
+        a.y[i] = mul_rn(o.mi, o.ri);
+        a.y2[i] = sub_rn(o.ri, acc);
+    } else if constexpr (MODE == RB_PRE1_RT) {
+        a.y[i] = mul_rn(o.mi, o.ri);
+        a.y2[i] = sub_rn(o.ri, acc);
+        a.y3[i] = o.ri;
+    } else if constexpr (MODE == RB_SMOOTH) {
+        a.y[i] = add_rn(o.xi, mul_rn(o.mi, sub_rn(o.ri, acc)));
+    } else if constexpr (MODE == RB_RESID) {
+        const T yi = sub_rn(o.ri, acc);
+        a.y[i] = yi;
+        if constexpr (ND >= 1) dv[0] = fma((double)yi, (double)yi, dv[0]);
+    } else if constexpr (MODE == RB_PROSMOOTH) {
+        const T xp = add_rn(o.xi, a.e[o.gi]);
+        a.y[i] = add_rn(xp, mul_rn(o.mi, sub_rn(o.ri, acc)));
+    } else if constexpr (MODE == RB_PROSMOOTH_E) {
+        const T xp = add_rn(o.xi, kc_e_at(a, ks, o.gi));
+        a.y[i] = add_rn(xp, mul_rn(o.mi, sub_rn(o.ri, acc)));
+    } else {  // RB_SPMV
+        a.y[i] = acc;
+        const double xd = (double)o.xi;
+        if constexpr (ND >= 1) dv[0] = fma(xd, (double)acc, dv[0]);
+        if constexpr (ND >= 2) dv[1] = fma(xd, (double)o.d1i, dv[1]);
+        if constexpr (ND >= 3) dv[2] = fma(xd, (double)o.d2i, dv[2]);
+    }
 }
 
 // Kernel entry: false when the kernel lies inside a skipped second K-cycle step.  A fused
@@ -218,6 +277,9 @@ template <typename T>
 int launch_rowblock(Handle* h, int mode, int ndots, const RBArgs<T>& a);
 template <typename T>
 int launch_rowblock_tma(Handle* h, int mode, int ndots, const RBArgs<T>& a);
+template <typename T>
+int launch_sell(Handle* h, int mode, int ndots, const RBArgs<T>& a);
+int build_sell(Handle* h, Level& L, bool mixed);
 
 template <typename T>
 int launch_restrict(Handle* h, int nc, const int* aggptr, const int* members, const T* s,

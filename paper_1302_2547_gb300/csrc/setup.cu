@@ -242,6 +242,9 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
                                       L.val32)))
             goto done;
     }
+    // sliced ELLPACK copies of the large levels (not the coarsest, which is solved densely)
+    for (int l = 0; h->p.sell_rows > 0 && l < h->nlev - 1; l++)
+        if (h->lev[l].n >= h->p.sell_rows && (st = build_sell(h, h->lev[l], mixed))) goto done;
     {  // coarsest level: its dense FP64 inverse
         Level& Lc = h->lev[h->nlev - 1];
         h->nco = Lc.n;
@@ -268,7 +271,8 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
         h->q = dalloc<double>(h, n0, &st);
         h->osc = dalloc<OuterScalars>(h, 1, &st);
         LevelScalars* sc = dalloc<LevelScalars>(h, h->nlev, &st);
-        long long pcap = (long long)grid_for(n0, kRowsPerBlock) * 3;
+        // partial sums of the widest reduction: three dots over blocks of at least 32 rows
+        long long pcap = (long long)grid_for(n0, 32) * 3;
         if (pcap < 16LL * h->num_sms) pcap = 16LL * h->num_sms;
         h->partials = dalloc<double>(h, pcap, &st);
         h->partials_cap = pcap;

@@ -18,12 +18,26 @@ template <>
 struct Prec<float> {
     static const float* val(const Level& L) { return L.val32; }
     static const float* minv(const Level& L) { return L.minv32; }
+    static const float* sell(const Level& L) { return L.sl_val32; }
 };
 template <>
 struct Prec<double> {
     static const double* val(const Level& L) { return L.val64; }
     static const double* minv(const Level& L) { return L.minv64; }
+    static const double* sell(const Level& L) { return L.sl_val64; }
 };
+
+// The level's sliced ELLPACK copy, when one was built for this precision.
+template <typename T>
+static void sell_args(RBArgs<T>& a, const Level& L) {
+    const T* v = Prec<T>::sell(L);
+    if (!L.sl_ptr || !v) return;
+    a.sptr = L.sl_ptr;
+    a.scol = L.sl_col;
+    a.sval = v;
+    a.slen = L.sl_len;
+    a.nslices = L.sl_ns;
+}
 
 // ---- profiling: events around level-0 launches of the selected kernel class ----------------
 static int prof_begin(Handle* h, int cls, int level) {
@@ -69,6 +83,7 @@ static RBArgs<T> rb_args(Handle* h, const Level& L) {
     a.partials = h->partials;
     a.counter = &h->ctrl->red_count;
     a.skip = &h->ctrl->skip;
+    sell_args<T>(a, L);
     return a;
 }
 
@@ -266,6 +281,7 @@ static int outer_iteration(Handle* h, bool to_host) {
         a.rowptr = L0.rowptr;
         a.col = L0.col;
         a.val = L0.val64;
+        sell_args<double>(a, L0);
         a.x = h->p_;
         a.y = h->q;
         a.d1 = h->r;
@@ -435,6 +451,7 @@ static int true_residual(Handle* h) {
     a.rowptr = L0.rowptr;
     a.col = L0.col;
     a.val = L0.val64;
+    sell_args<double>(a, L0);
     a.x = h->x;
     a.r = h->b;
     a.y = h->r;

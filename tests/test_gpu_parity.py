@@ -218,6 +218,45 @@ def test_tma_rowblock_path(oracle, precision):
             U.uaamg_free(h)
 
 
+@pytest.mark.parametrize("precision", [U.UAAMG_FP64, U.UAAMG_MIXED])
+def test_sell_path(oracle, precision):
+    """Every level that qualifies keeps a sliced ELLPACK copy (sell_rows=1).  The two-level B
+    (no inner products) must equal, bit for bit, the one-thread-per-row TMA kernels
+    (tma_rows=1): both add each row in stored order.  Solves meet the solve bars, on a grid
+    (uniform rows) and on a random geometric graph (rows of varying length, where a level
+    may skip the copy for its padding)."""
+    A = I.grid3d(16, sigma=0.25, seed=8)
+    kw = dict(precision=precision, max_levels=2, coarse_size=64, max_agg_size=0, agg_repeat=2)
+    hs = U.uaamg_setup(A.rowptr, A.col, A.val, U.uaamg_default_params(sell_rows=1, **kw))
+    ht = U.uaamg_setup(A.rowptr, A.col, A.val, U.uaamg_default_params(tma_rows=1, **kw))
+    try:
+        r = np.random.default_rng(6).standard_normal(A.n)
+        gs, gt = U.uaamg_apply_B(hs, 0, r), U.uaamg_apply_B(ht, 0, r)
+        assert np.array_equal(bits(gs), bits(gt))
+    finally:
+        U.uaamg_free(hs)
+        U.uaamg_free(ht)
+    for A in (I.grid3d(30, sigma=0.25, seed=5), I.rgg(20000, 8.0, seed=3)):
+        tol = 1e-8
+        h, H, _ = both(A, oracle, precision=precision, sell_rows=1, max_agg_size=0)
+        try:
+            b = I.rhs_uniform(A.n, 2000)
+            x = np.zeros(A.n)
+            st, it, rr = U.uaamg_solve(h, b, x, tol)
+            xo, ito, rro, sto, _ = H.solve(b, tol)
+            assert st == 0 and sto == 0
+            Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+            bn = np.linalg.norm(b)
+            assert np.linalg.norm(b - Asp @ x) <= tol * bn * 1.0001
+            assert np.linalg.norm(Asp @ (x - xo)) <= 2.0001 * tol * bn
+            if precision == U.UAAMG_FP64:
+                assert abs(it - ito) <= 1, (it, ito)
+            else:
+                assert it <= ito + 5, (it, ito)
+        finally:
+            U.uaamg_free(h)
+
+
 SOLVE_CASES = [
     ("poisson2d_64", lambda: I.poisson2d_64(), {}),
     ("grid3d_32", lambda: I.grid3d(32, sigma=0.25, seed=1), {"max_agg_size": 0}),
