@@ -355,6 +355,85 @@ def run_gpu(args, rank, world):
     return out
 
 
+def run_serving(n_requests=120, seed=2024):
+    """The solve service (uaamg_server_*) under a Poisson stream of requests, shaped like the
+    serving workload with smaller sizes so that it runs in seconds: 12 matrices (2D grid, 3D
+    grid with lognormal weights, random geometric graph of mean degree 8), sizes
+    log-uniform in [1e4, 1e6]; 30% of the requests repeat an already seen matrix (cached
+    hierarchy, new right-hand side), the rest bring a matrix the cache has not seen (new
+    key: a setup).  The arrival rate is 70% of the capacity measured one request at a time.
+    Latency = the server's time from submit to result."""
+    from paper_1302_2547_gb300 import _lib as U
+    from paper_1302_2547_gb300 import inputs as I
+
+    rng = np.random.default_rng(seed)
+    pool = []
+    for k in range(12):
+        n = int(np.exp(rng.uniform(np.log(1e4), np.log(1e6))))
+        if k % 3 == 0:
+            A = I.grid2d(max(8, int(round(np.sqrt(n)))))
+        elif k % 3 == 1:
+            A = I.grid3d(max(4, int(round(n ** (1.0 / 3.0)))), sigma=0.25, seed=3000 + k)
+        else:
+            A = I.rgg(n, 8.0, seed=3000 + k)
+        pool.append(A)
+    srv = U.Server(U.uaamg_default_params(**BENCH_PARAMS), budget_bytes=150 << 30, workers=4,
+                   max_batch=16)
+    next_key = [1]
+
+    def submit(m, key=None):
+        A = pool[m]
+        if key is None:
+            key = next_key[0]
+            next_key[0] += 1
+        b = rng.uniform(-1.0, 1.0, A.n)
+        return srv.submit(A.rowptr, A.col, A.val, b, TOL, key=key), key
+
+    try:
+        # capacity: requests with new matrices, one at a time
+        t0 = time.perf_counter()
+        for m in range(len(pool)):
+            t, _ = submit(m)
+            st, _, _, rr, _, _ = srv.wait(t)
+            if st != 0:
+                raise RuntimeError(f"serving warm-up status {st}")
+        service = (time.perf_counter() - t0) / len(pool)
+        lam = 0.7 / service
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, n_requests))
+        seen = []  # (matrix, key) pairs whose hierarchy the server holds
+        tickets = []
+        new = 0
+        t0 = time.perf_counter()
+        for a in arrivals:
+            d = t0 + a - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            if seen and rng.uniform() < 0.3:
+                m, key = seen[int(rng.integers(0, len(seen)))]
+                t, _ = submit(m, key)
+            else:
+                m = int(rng.integers(0, len(pool)))
+                t, key = submit(m)
+                seen.append((m, key))
+                new += 1
+            tickets.append(t)
+        res = [srv.wait(t) for t in tickets]
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+    finally:
+        srv.close()
+    lat = np.array([r[4] for r in res])
+    failed = sum(1 for r in res if r[0] != 0 or not (r[3] <= TOL))
+    return {"requests": n_requests, "lambda_per_s": round(lam, 2), "offered_load": 0.7,
+            "new_matrix_fraction": round(new / n_requests, 3),
+            "p50_ms": round(float(np.percentile(lat, 50)), 2),
+            "p99_ms": round(float(np.percentile(lat, 99)), 2),
+            "solves_per_s": round(n_requests / wall, 2), "failed": failed,
+            "batches": stats["batches"], "cache_hits": stats["cache_hits"],
+            "setups": stats["setups"], "workers": 4, "max_batch": 16,
+            "sizes": "log-uniform 1e4-1e6; 2D grid, 3D grid, RGG (mean degree 8)"}
+
+
 def run_cpu_baseline(sample_steps=1):
     """The oracle as it stands (serial C, FP64) on the same workload: setup + solve."""
     from oracle import oracle as O
@@ -388,6 +467,8 @@ def main():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-plain", action="store_true", help="do not time the FP64 path")
     ap.add_argument("--skip-batched", action="store_true", help="do not time solve_many")
+    ap.add_argument("--skip-serving", action="store_true",
+                    help="do not run the solve service under a request stream")
     ap.add_argument("--tma-rows", type=int, default=None,
                     help="row threshold of the TMA-staged row-block kernels (0 = off)")
     ap.add_argument("--fuse-below", type=int, default=None,
@@ -438,6 +519,11 @@ def main():
         dist.barrier()
     out = run_gpu(args, rank, world)
     if rank == 0:
+        if world == 1 and not args.skip_serving:
+            try:
+                out["serving"] = run_serving()
+            except Exception as e:  # reported, not hidden: the main line still stands
+                out["serving"] = {"error": f"{type(e).__name__}: {e}"}
         if world == 1 and not args.skip_cpu_baseline:
             out["cpu_baseline"] = run_cpu_baseline(1)[0]
         print(json.dumps(out))
