@@ -207,6 +207,34 @@ __device__ __forceinline__ long long global_ns() {
     return t;
 }
 
+// Programmatic dependent launch (small-level kernels): a kernel launched with the
+// programmatic-serialization attribute may start while its predecessor on the stream still
+// runs; pdl_wait() blocks until that predecessor has completed and its writes are visible,
+// and must precede every read of them.  pdl_trigger() lets this kernel's own successor
+// start launching.  Both are no-ops for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+constexpr int kPdlMaxRows = 65536;  // levels up to this size launch with the attribute
+
+// Launch, with the programmatic-serialization attribute when `pdl`.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -40,6 +40,8 @@ constexpr int kGrp = 2;  // four-entry groups a thread loads per batch
 
 template <typename T, int MODE, int ND>
 __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
+    pdl_wait();
+    pdl_trigger();
     if (!rb_enter<T, MODE>(a)) return;
     const KScal<T> ks = kscal<T, MODE>(a);
     __shared__ T sval[kChunk];
@@ -158,9 +160,10 @@ int launch_rowblock(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
     cudaStream_t st = h->work;
 #define RB_CASE(M, D)                                                 \
     if (mode == M && ndots == D) {                                    \
-        k_rowblock<T, M, D><<<grid, kThreads, 0, st>>>(a);            \
+        cudaError_t e = launch_k(a.n <= kPdlMaxRows, k_rowblock<T, M, D>, dim3(grid), \
+                                 dim3(kThreads), 0, st, a);                          \
         count_launch(h);                                              \
-        return check_cuda(cudaGetLastError());                        \
+        return check_cuda(e);                                         \
     }
     RB_CASE(RB_PRE1, 0)
     RB_CASE(RB_PRE1_RT, 0)
@@ -187,6 +190,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_restrict(int nc, const int* __restrict__ aggptr, const int* __restrict__ members,
            const T* __restrict__ s, T* __restrict__ rc, const int* skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip && *(volatile const int*)skip) return;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
@@ -198,9 +203,10 @@ k_restrict(int nc, const int* __restrict__ aggptr, const int* __restrict__ membe
 template <typename T>
 int launch_restrict(Handle* h, int nc, const int* aggptr, const int* members, const T* s,
                     T* rc, const int* skip) {
-    k_restrict<T><<<grid_for(nc, kThreads), kThreads, 0, h->work>>>(nc, aggptr, members, s, rc, skip);
+    cudaError_t e = launch_k(nc <= kPdlMaxRows, k_restrict<T>, dim3(grid_for(nc, kThreads)),
+                             dim3(kThreads), 0, h->work, nc, aggptr, members, s, rc, skip);
     count_launch(h);
-    return check_cuda(cudaGetLastError());
+    return check_cuda(e);
 }
 template int launch_restrict<float>(Handle*, int, const int*, const int*, const float*, float*, const int*);
 template int launch_restrict<double>(Handle*, int, const int*, const int*, const double*, double*, const int*);
@@ -212,6 +218,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_dense_apply(int n, const double* __restrict__ inv, const T* __restrict__ in,
               T* __restrict__ out, const int* skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip && *(volatile const int*)skip) return;
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -225,9 +233,10 @@ k_dense_apply(int n, const double* __restrict__ inv, const T* __restrict__ in,
 template <typename T>
 int launch_dense_apply(Handle* h, int n, const double* inv, const T* in, T* out,
                        const int* skip) {
-    k_dense_apply<T><<<grid_for((long long)n * 32, kThreads), kThreads, 0, h->work>>>(n, inv, in, out, skip);
+    cudaError_t e = launch_k(true, k_dense_apply<T>, dim3(grid_for((long long)n * 32, kThreads)),
+                             dim3(kThreads), 0, h->work, n, inv, in, out, skip);
     count_launch(h);
-    return check_cuda(cudaGetLastError());
+    return check_cuda(e);
 }
 template int launch_dense_apply<float>(Handle*, int, const double*, const float*, float*, const int*);
 template int launch_dense_apply<double>(Handle*, int, const double*, const double*, double*, const int*);
@@ -245,6 +254,8 @@ template <typename T, bool TAU>
 __global__ void __launch_bounds__(kThreads)
 k_kc_rt(int level, int n, const T* __restrict__ rho, const T* __restrict__ v1, T* __restrict__ rt,
         LevelScalars* sc, int inner, double tau, Ctrl* ctrl, double* partials) {
+    pdl_wait();
+    pdl_trigger();
     if (*(volatile const int*)&ctrl->skip) return;
     const bool ok = sc->rho1 > 0.0;
     const T a1t = (T)sc->a1;  // alpha1 / rho1, set by the first SpMV's last block
@@ -287,8 +298,11 @@ int launch_kc_rt(Handle* h, int level, int n, const T* rho, const T* v1, T* rt,
         k_kc_tau<<<1, 32, 0, h->work>>>(level, sc, tau, ctrl);
         count_launch(h, 2);
     } else {
-        k_kc_rt<T, false><<<grid, kThreads, 0, h->work>>>(level, n, rho, v1, rt, sc, inner, tau, ctrl, h->partials);
+        cudaError_t e = launch_k(n <= kPdlMaxRows, k_kc_rt<T, false>, dim3(grid), dim3(kThreads),
+                                 0, h->work, level, n, rho, v1, rt, sc, inner, tau, ctrl,
+                                 h->partials);
         count_launch(h);
+        if (e != cudaSuccess) return check_cuda(e);
     }
     return check_cuda(cudaGetLastError());
 }
@@ -299,6 +313,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_kc_combine(int level, int n, const T* __restrict__ c1, const T* __restrict__ c2,
              T* __restrict__ e, const LevelScalars* sc, Ctrl* ctrl) {
+    pdl_wait();
+    pdl_trigger();
     const int sk = *(volatile const int*)&ctrl->skip;
     if (sk != 0 && sk != level + 1) return;  // inside an ancestor's skipped step
     const double w1 = sc->w1, w2 = sc->w2;    // set by the step SpMVs' last blocks
@@ -318,9 +334,10 @@ int launch_kc_combine(Handle* h, int level, int n, const T* c1, const T* c2, T* 
                       const LevelScalars* sc, Ctrl* ctrl) {
     int grid = grid_for(n, kThreads);
     if (grid > 8 * h->num_sms) grid = 8 * h->num_sms;
-    k_kc_combine<T><<<grid, kThreads, 0, h->work>>>(level, n, c1, c2, e, sc, ctrl);
+    cudaError_t err = launch_k(n <= kPdlMaxRows, k_kc_combine<T>, dim3(grid), dim3(kThreads), 0,
+                               h->work, level, n, c1, c2, e, sc, ctrl);
     count_launch(h);
-    return check_cuda(cudaGetLastError());
+    return check_cuda(err);
 }
 template int launch_kc_combine<float>(Handle*, int, int, const float*, const float*, float*, const LevelScalars*, Ctrl*);
 template int launch_kc_combine<double>(Handle*, int, int, const double*, const double*, double*, const LevelScalars*, Ctrl*);
@@ -330,6 +347,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_prolong(int n, const T* __restrict__ x, const int* __restrict__ agg, const T* __restrict__ e,
           T* __restrict__ y, const int* skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip && *(volatile const int*)skip) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = x ? add_rn(x[i], e[agg[i]]) : e[agg[i]];
@@ -338,9 +357,10 @@ k_prolong(int n, const T* __restrict__ x, const int* __restrict__ agg, const T* 
 template <typename T>
 int launch_prolong(Handle* h, int n, const T* x, const int* agg, const T* e, T* y,
                    const int* skip) {
-    k_prolong<T><<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, x, agg, e, y, skip);
+    cudaError_t err = launch_k(n <= kPdlMaxRows, k_prolong<T>, dim3(grid_for(n, kThreads)),
+                               dim3(kThreads), 0, h->work, n, x, agg, e, y, skip);
     count_launch(h);
-    return check_cuda(cudaGetLastError());
+    return check_cuda(err);
 }
 template int launch_prolong<float>(Handle*, int, const float*, const int*, const float*, float*, const int*);
 template int launch_prolong<double>(Handle*, int, const double*, const int*, const double*, double*, const int*);
