@@ -33,6 +33,11 @@ WORKLOAD = "laplace3d_128^3 7-point, Dirichlet, lognormal(0.25) edge weights"
 # twice per level (Section 3.3), one flexible-CG step on levels reached by coarsening
 # weaker than 5x, and a small level that shrinks by less than 1.5x becomes the coarsest.
 BENCH_PARAMS = dict(max_agg_size=4, agg_repeat=2, kcycle_ratio=5.0, min_coarsening=1.5)
+# The unstructured workload (4M-point random geometric graph, mean degree 8): aggregates of
+# unbounded size, one aggregation per level, one K-cycle step below 3x coarsening.  With a
+# size limit the coarse levels of this graph stall (about 2% per level below a few
+# thousand vertices).
+RGG_PARAMS = dict(max_agg_size=0, agg_repeat=1, kcycle_ratio=3.0, min_coarsening=1.5)
 
 # DRAM traffic per launch of each roofline kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the sources that
@@ -355,6 +360,49 @@ def run_gpu(args, rank, world):
     return out
 
 
+def run_rgg(steps=3, warmup=1):
+    """Setup + mixed solve of the 4M-point random geometric graph (inputs resident), timed
+    like the main line; reported beside it, not as the headline."""
+    import torch
+    import scipy.sparse as sp
+
+    from paper_1302_2547_gb300 import _lib as U
+    from paper_1302_2547_gb300 import inputs as I
+
+    A = I.rgg_4m()
+    dev = torch.device("cuda:0")
+    rp, cc, vv = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+    b = torch.from_numpy(I.rhs_uniform(A.n, I.RHS_SEED + 2)).to(dev)
+    x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    p = U.uaamg_default_params(**RGG_PARAMS)
+    rec = []
+    for k in range(warmup + steps):
+        x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h = U.uaamg_setup(rp, cc, vv, p)
+        st, it, rr = U.uaamg_solve(h, b, x, TOL)
+        s = U.uaamg_get_stats(h)
+        nlev = U.uaamg_num_levels(h)
+        U.uaamg_free(h)
+        e1.record()
+        torch.cuda.synchronize()
+        if st != 0:
+            raise RuntimeError(f"rgg solve status {st}")
+        if k >= warmup:
+            rec.append((e0.elapsed_time(e1), s, it))
+    Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+    xb, bb = x.cpu().numpy(), b.cpu().numpy()
+    ms = float(np.median([r[0] for r in rec]))
+    return {"workload": f"rgg 4M points, mean degree 8, LCC n={A.n}, nnz={A.nnz}",
+            "params": RGG_PARAMS, "levels": nlev, "iterations": rec[-1][2],
+            "solves_per_s": round(1000.0 / ms, 3), "ms_per_step": round(ms, 3),
+            "setup_ms": round(float(np.median([r[1]["setup_ms"] for r in rec])), 3),
+            "solve_ms": round(float(np.median([r[1]["solve_ms"] for r in rec])), 3),
+            "relres_host_fp64": float(np.linalg.norm(bb - Asp @ xb) / np.linalg.norm(bb))}
+
+
 def run_serving(n_requests=120, seed=2024):
     """The solve service (uaamg_server_*) under a Poisson stream of requests, shaped like the
     serving workload with smaller sizes so that it runs in seconds: 12 matrices (2D grid, 3D
@@ -469,6 +517,8 @@ def main():
     ap.add_argument("--skip-batched", action="store_true", help="do not time solve_many")
     ap.add_argument("--skip-serving", action="store_true",
                     help="do not run the solve service under a request stream")
+    ap.add_argument("--rgg", action="store_true",
+                    help="also time the 4M-point random geometric graph (about a minute)")
     ap.add_argument("--tma-rows", type=int, default=None,
                     help="row threshold of the TMA-staged row-block kernels (0 = off)")
     ap.add_argument("--fuse-below", type=int, default=None,
@@ -519,6 +569,8 @@ def main():
         dist.barrier()
     out = run_gpu(args, rank, world)
     if rank == 0:
+        if world == 1 and args.rgg:
+            out["rgg_4m"] = run_rgg()
         if world == 1 and not args.skip_serving:
             try:
                 out["serving"] = run_serving()

@@ -425,18 +425,18 @@ def test_device_pointers_and_streams(oracle):
         U.uaamg_free(h)
 
 
-@pytest.mark.parametrize("which", ["laplace3d_128"])
+@pytest.mark.parametrize("which", ["laplace3d_128", "rgg_4m"])
 def test_full_size_parity(oracle, which):
-    """The benchmark workload at full size, device-resident inputs as the benchmark passes
-    them: the whole hierarchy bit-exact, and the mixed-precision solve to 1e-8."""
+    """The full-size workloads, device-resident inputs as the benchmark passes them: the
+    whole hierarchy bit-exact, and the mixed-precision solve to 1e-8."""
     import torch
 
-    A = I.laplace3d_128()
+    from bench import BENCH_PARAMS, RGG_PARAMS
+
+    A, kw = (I.laplace3d_128(), BENCH_PARAMS) if which == "laplace3d_128" else (I.rgg_4m(), RGG_PARAMS)
     dev = torch.device("cuda:0")
     rp, cc, vv = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
-    from bench import BENCH_PARAMS
-
-    p = U.uaamg_default_params(**BENCH_PARAMS)
+    p = U.uaamg_default_params(**kw)
     h = U.uaamg_setup(rp, cc, vv, p)
     H = oracle.Hierarchy(A.rowptr, A.col, A.val,
                          oracle.Params(**{k: getattr(p, k) for k in OR_KEYS}))
