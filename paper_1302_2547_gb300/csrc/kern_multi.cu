@@ -85,6 +85,8 @@ inline int mgrid(const Handle* h, int n, const MGeom& g) {
 
 template <typename T, int MODE, int ND>
 __global__ void __launch_bounds__(kThreads) k_mrow(MArgs<T> a) {
+    pdl_wait();
+    pdl_trigger();
     const MGeom g = mgeom(a.R);
     const int lr = threadIdx.x & (g.Rp - 1);
     const int R = a.R;
@@ -135,9 +137,10 @@ int launch_mrow(Handle* h, int mode, int ndots, const MArgs<T>& a) {
     cudaStream_t st = h->work;
 #define MR_CASE(M, D)                                       \
     if (mode == M && ndots == D) {                          \
-        k_mrow<T, M, D><<<grid, kThreads, 0, st>>>(a);      \
+        cudaError_t e = launch_k(a.n <= kPdlMaxRows, k_mrow<T, M, D>, dim3(grid), \
+                                 dim3(kThreads), 0, st, a);                      \
         count_launch(h);                                    \
-        return check_cuda(cudaGetLastError());              \
+        return check_cuda(e);                               \
     }
     MR_CASE(RB_PRE1, 0)
     MR_CASE(RB_SMOOTH, 0)
@@ -156,6 +159,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_mrestrict(int nc, int R, const int* __restrict__ aggptr, const int* __restrict__ members,
             const T* __restrict__ s, T* __restrict__ rc) {
+    pdl_wait();
+    pdl_trigger();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)nc * R) return;
     const int I = (int)(t / R), r = (int)(t % R);
@@ -165,28 +170,50 @@ k_mrestrict(int nc, int R, const int* __restrict__ aggptr, const int* __restrict
     rc[t] = sum;
 }
 
+// Coarsest solve for R columns: out[i][r] = sum_j inv[i][j] in[j][r] in FP64.  One block
+// per row i; its threads split j into 256/Rp chunks for each column, and the chunks' sums
+// are added in chunk order in shared memory (a fixed order, so the result is deterministic).
+// Spreading the rows over blocks keeps the FP64 work on many SMs.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_mdense(int n, int R, const double* __restrict__ inv, const T* __restrict__ in,
          T* __restrict__ out) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)n * R) return;
-    const int i = (int)(t / R), r = (int)(t % R);
+    pdl_wait();
+    pdl_trigger();
+    __shared__ double part[kThreads];
+    const MGeom g = mgeom(R);
+    const int i = blockIdx.x;
+    const int r = threadIdx.x & (g.Rp - 1);
+    const int jc = threadIdx.x >> g.lgRp;
+    const int nchunks = kThreads >> g.lgRp;
     double s = 0.0;
-    for (int j = 0; j < n; j++) s += inv[(size_t)i * n + j] * (double)in[(size_t)j * R + r];
-    out[t] = (T)s;
+    if (r < R)
+        for (int j = jc; j < n; j += nchunks)
+            s = fma(inv[(size_t)i * n + j], (double)in[(size_t)j * R + r], s);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if ((int)threadIdx.x < R) {
+        double t = 0.0;
+        for (int c = 0; c < nchunks; c++) t += part[(c << g.lgRp) + threadIdx.x];
+        out[(size_t)i * R + threadIdx.x] = (T)t;
+    }
 }
 
 template <typename T>
 int launch_mrestrict(Handle* h, int nc, int R, const int* aggptr, const int* members,
                      const T* s, T* rc) {
-    k_mrestrict<T><<<grid_for((long long)nc * R, kThreads), kThreads, 0, h->work>>>(nc, R, aggptr, members, s, rc);
+    cudaError_t e = launch_k(nc <= kPdlMaxRows, k_mrestrict<T>,
+                             dim3(grid_for((long long)nc * R, kThreads)), dim3(kThreads), 0,
+                             h->work, nc, R, aggptr, members, s, rc);
+    if (e != cudaSuccess) return check_cuda(e);
     count_launch(h);
     return check_cuda(cudaGetLastError());
 }
 template <typename T>
 int launch_mdense(Handle* h, int n, int R, const double* inv, const T* in, T* out) {
-    k_mdense<T><<<grid_for((long long)n * R, kThreads), kThreads, 0, h->work>>>(n, R, inv, in, out);
+    cudaError_t e = launch_k(true, k_mdense<T>, dim3(n), dim3(kThreads), 0, h->work, n, R, inv,
+                             in, out);
+    if (e != cudaSuccess) return check_cuda(e);
     count_launch(h);
     return check_cuda(cudaGetLastError());
 }
@@ -204,6 +231,8 @@ template <typename T, bool TAU>
 __global__ void __launch_bounds__(kThreads)
 k_mkc_rt(int n, int R, const T* __restrict__ rho, const T* __restrict__ v1, T* __restrict__ rt,
          double* sc, double* partials, unsigned int* counter) {
+    pdl_wait();
+    pdl_trigger();
     const MGeom g = mgeom(R);
     const int lr = threadIdx.x & (g.Rp - 1);
     double dv[2] = {0.0, 0.0};
@@ -232,6 +261,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_mkc_combine(int n, int R, const T* __restrict__ c1, const T* __restrict__ c2,
               T* __restrict__ e, const double* sc, int second, double tau) {
+    pdl_wait();
+    pdl_trigger();
     const MGeom g = mgeom(R);
     const int lr = threadIdx.x & (g.Rp - 1);
     const int i = blockIdx.x * g.rows_per_block + (threadIdx.x >> g.lgRp);
@@ -273,7 +304,12 @@ int launch_mkc_rt(Handle* h, int n, int R, const T* rho, const T* v1, T* rt, dou
     if (tau)
         k_mkc_rt<T, true><<<grid, kThreads, 0, h->work>>>(n, R, rho, v1, rt, sc, h->partials, &h->ctrl->red_count);
     else
-        k_mkc_rt<T, false><<<grid, kThreads, 0, h->work>>>(n, R, rho, v1, rt, sc, h->partials, &h->ctrl->red_count);
+        {
+            cudaError_t e = launch_k(n <= kPdlMaxRows, k_mkc_rt<T, false>, dim3(grid),
+                                     dim3(kThreads), 0, h->work, n, R, rho, v1, rt, sc,
+                                     h->partials, &h->ctrl->red_count);
+            if (e != cudaSuccess) return check_cuda(e);
+        }
     count_launch(h);
     return check_cuda(cudaGetLastError());
 }
@@ -281,7 +317,10 @@ template <typename T>
 int launch_mkc_combine(Handle* h, int n, int R, const T* c1, const T* c2, T* e,
                        const double* sc, int second, double tau) {
     const MGeom g = mgeom(R);
-    k_mkc_combine<T><<<grid_for(n, g.rows_per_block), kThreads, 0, h->work>>>(n, R, c1, c2, e, sc, second, tau);
+    cudaError_t err = launch_k(n <= kPdlMaxRows, k_mkc_combine<T>,
+                               dim3(grid_for(n, g.rows_per_block)), dim3(kThreads), 0, h->work,
+                               n, R, c1, c2, e, sc, second, tau);
+    if (err != cudaSuccess) return check_cuda(err);
     count_launch(h);
     return check_cuda(cudaGetLastError());
 }

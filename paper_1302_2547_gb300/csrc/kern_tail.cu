@@ -4,7 +4,7 @@
 // with one-step levels), and on small levels every step is a sub-microsecond kernel, so the
 // cycle becomes launch-bound.  From the first level with at most kTailMaxN unknowns down
 // to the coarsest, this kernel runs the whole recursion K_m -> B_m -> K_{m+1} ... in one
-// thread block of 1024 threads: each step of the launched path (fused SpMV + l1-Jacobi
+// thread block of 512 threads: each step of the launched path (fused SpMV + l1-Jacobi
 // sweeps, residual restriction, prolongation, the two flexible-CG steps and the exact
 // coarsest solve) becomes a block-wide phase separated by __syncthreads, with the same
 // arithmetic per entry and block-level fixed-order reductions for the inner products.
@@ -14,7 +14,7 @@
 
 namespace uaamg {
 
-constexpr int kTailThreads = 1024;
+constexpr int kTailThreads = 512;
 
 // Block-wide fixed-order sum of ND values; every thread receives the totals.
 template <int ND>
@@ -49,14 +49,35 @@ struct TailFrame {
 };
 constexpr int kTailMaxFrames = 2 * kMaxLevels;
 
+constexpr int kTailBatch = 8;  // entries whose gathers a thread has in flight
+
+// Row i's sum of val[k] g(col[k]) over its entries, in stored order, with the gathers of
+// kTailBatch entries issued before the first is used.
+template <typename T, typename G>
+__device__ __forceinline__ T tail_row(const TailLevel& L, int i, G g) {
+    const T* val = (const T*)L.val;
+    const int k1 = L.rowptr[i + 1];
+    T acc = T(0);
+    for (int k = L.rowptr[i]; k < k1; k += kTailBatch) {
+        T xg[kTailBatch], vv[kTailBatch];
+#pragma unroll
+        for (int u = 0; u < kTailBatch; u++) {
+            const bool in = k + u < k1;
+            xg[u] = in ? g(L.col[k + u]) : T(0);
+            vv[u] = in ? val[k + u] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kTailBatch; u++)
+            if (k + u < k1) acc = fma_rn(vv[u], xg[u], acc);
+    }
+    return acc;
+}
+
 template <typename T>
 __device__ __forceinline__ void spmv_rows(const TailLevel& L, const T* x, T* y, int nd,
                                           const T* da, const T* db, double* d) {
-    const T* val = (const T*)L.val;
     for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
-        T acc = T(0);
-        for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; k++)
-            acc = fma_rn(val[k], x[L.col[k]], acc);
+        const T acc = tail_row<T>(L, i, [&](int j) { return x[j]; });
         y[i] = acc;
         const double xi = (double)x[i];
         d[0] += xi * (double)acc;
@@ -89,11 +110,14 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
         double rho1 = f.rho1, w1 = f.w1, w2 = f.w2;
         if (f.kind == 0) {  // ---- K_m: two flexible-CG steps preconditioned by B_m ----
             T *c1 = (T*)L.c1, *v1 = (T*)L.v1, *rt = (T*)L.rt, *c2 = (T*)L.c2, *v2 = (T*)L.v2;
-            if (f.level == nlev - 1) {  // exact solve with the dense inverse
-                for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
+            if (f.level == nlev - 1) {  // exact solve with the dense inverse, a warp per row
+                const int lane = threadIdx.x & 31;
+                for (int i = threadIdx.x >> 5; i < L.n; i += kTailThreads / 32) {
                     double sum = 0.0;
-                    for (int j = 0; j < L.n; j++) sum += inv[(size_t)i * L.n + j] * (double)in[j];
-                    out[i] = (T)sum;
+                    for (int j = lane; j < L.n; j += 32)
+                        sum = fma(inv[(size_t)i * L.n + j], (double)in[j], sum);
+                    sum = warp_sum(sum);
+                    if (lane == 0) out[i] = (T)sum;
                 }
                 pop = 1;
             } else if (f.phase == 0) {  // c1 = B_m(rho)
@@ -153,7 +177,6 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
             }
         } else {  // ---- B_l: pre-sweep, restriction, K_{l+1}, prolongation + post-sweep ----
             const TailLevel& C = lv[f.level + 1];
-            const T* val = (const T*)L.val;
             const T* minv = (const T*)L.minv;
             T* x = (T*)L.w;
             T* s = (T*)L.s;
@@ -161,19 +184,23 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
             T* ec = (T*)C.out;
             if (f.phase == 0) {
                 for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
-                    T acc = T(0);
-                    for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; k++) {
-                        const int j = L.col[k];
-                        acc = fma_rn(val[k], mul_rn(minv[j], in[j]), acc);
-                    }
+                    const T acc = tail_row<T>(L, i, [&](int j) { return mul_rn(minv[j], in[j]); });
                     x[i] = mul_rn(minv[i], in[i]);
                     s[i] = sub_rn(in[i], acc);
                 }
                 __syncthreads();
                 for (int I = threadIdx.x; I < C.n; I += kTailThreads) {
+                    const int q1 = L.aggptr[I + 1];
                     T sum = T(0);
-                    for (int q = L.aggptr[I]; q < L.aggptr[I + 1]; q++)
-                        sum = add_rn(sum, s[L.members[q]]);
+                    for (int q = L.aggptr[I]; q < q1; q += kTailBatch) {
+                        T sv[kTailBatch];
+#pragma unroll
+                        for (int u = 0; u < kTailBatch; u++)
+                            sv[u] = q + u < q1 ? s[L.members[q + u]] : T(0);
+#pragma unroll
+                        for (int u = 0; u < kTailBatch; u++)
+                            if (q + u < q1) sum = add_rn(sum, sv[u]);
+                    }
                     rc[I] = sum;
                 }
                 child = TailFrame{0, f.level + 1, 0, rc, ec, 0.0, 0.0, 0.0};
@@ -181,11 +208,7 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
                 next_phase = 1;
             } else {
                 for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
-                    T acc = T(0);
-                    for (int k = L.rowptr[i]; k < L.rowptr[i + 1]; k++) {
-                        const int j = L.col[k];
-                        acc = fma_rn(val[k], add_rn(x[j], ec[L.agg[j]]), acc);
-                    }
+                    const T acc = tail_row<T>(L, i, [&](int j) { return add_rn(x[j], ec[L.agg[j]]); });
                     const T xi = add_rn(x[i], ec[L.agg[i]]);
                     out[i] = add_rn(xi, mul_rn(minv[i], sub_rn(in[i], acc)));
                 }
