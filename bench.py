@@ -49,9 +49,11 @@ NCU_SOURCES = {
     "coarse": ("kern_setup.cu", "kernels.cuh", "common.cuh"),
 }
 NCU_TRAFFIC = {
-    # k_rowblock_tma<float, RB_PRE1> on level 0 of the 128^3 system, ncu --set full
-    # (profiles/rowblock_tma_laplace3d_128_level0.md): 141,838,336 + 8,989,952 bytes
-    ("smooth0", "2ef10e578243be6c"): 150828288,
+    # level 0 of the 128^3 system, ncu --set full (profiles/rowwarp_tma_laplace3d_128_level0.md)
+    # k_rowwarp_tma<float, RB_PRE1>: 141,839,360 + 7,679,232 bytes
+    ("smooth0", "6a34aba347144b4a"): 149518592,
+    # k_rowwarp_tma<double, RB_SPMV, 2 dots>: 216,976,128 + 12,992,256 bytes
+    ("spmv64", "6a34aba347144b4a"): 229968384,
 }
 
 
