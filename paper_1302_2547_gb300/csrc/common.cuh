@@ -1,5 +1,6 @@
 // common.cuh -- types and device helpers shared by the CUDA sources of libuaamg.
 #pragma once
+#include <atomic>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -206,6 +207,18 @@ __device__ __forceinline__ long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+
+// A launch property (occupancy, an attribute set) computed once per device and read from
+// any host thread (the solve service runs setups and solves on several threads).
+struct DevCache {
+    std::atomic<int> v[64];
+    int get(int dev) const {
+        return (dev >= 0 && dev < 64) ? v[dev].load(std::memory_order_relaxed) : 0;
+    }
+    void set(int dev, int x) {
+        if (dev >= 0 && dev < 64) v[dev].store(x, std::memory_order_relaxed);
+    }
+};
 
 // Programmatic dependent launch (small-level kernels): a kernel launched with the
 // programmatic-serialization attribute may start while its predecessor on the stream still

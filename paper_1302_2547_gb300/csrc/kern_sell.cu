@@ -144,15 +144,16 @@ __global__ void __launch_bounds__(kThreads) k_sell(RBArgs<T> a) {
 // final reduction, and each warp keeps several slices' loads coming.
 template <typename T, int MODE, int ND>
 static int launch_sell_one(Handle* h, const RBArgs<T>& a) {
-    static int per_sm[64] = {0};
-    const int dev = h->device < 64 ? h->device : 0;
-    if (!per_sm[dev]) {
+    static DevCache occ;
+    int per_sm = occ.get(h->device);
+    if (!per_sm) {
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sell<T, MODE, ND>, kThreads, 0);
-        per_sm[dev] = b > 0 ? b : 1;
+        per_sm = b > 0 ? b : 1;
+        occ.set(h->device, per_sm);
     }
     int grid = grid_for(a.nslices, kThreads / 32);
-    if (grid > per_sm[dev] * h->num_sms) grid = per_sm[dev] * h->num_sms;
+    if (grid > per_sm * h->num_sms) grid = per_sm * h->num_sms;
     k_sell<T, MODE, ND><<<grid, kThreads, 0, h->work>>>(a);
     count_launch(h);
     return check_cuda(cudaGetLastError());

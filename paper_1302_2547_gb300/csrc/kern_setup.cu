@@ -644,12 +644,14 @@ constexpr int kPaaLanesMaxN = 32768;  // largest level that shares lanes over a 
 
 template <int G>
 static int launch_paa_sr(Handle* h, const PaaArgs& a, int* grid) {
-    static int blocks_per_sm = 0;
+    static DevCache occ;
+    int blocks_per_sm = occ.get(h->device);
     if (!blocks_per_sm) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_paa_sr<G>,
                                                           kPaaThreads, 0) != cudaSuccess ||
             blocks_per_sm < 1)
             blocks_per_sm = 1;
+        occ.set(h->device, blocks_per_sm);
     }
     *grid = blocks_per_sm * h->num_sms;
     const int need = grid_for((long long)a.n * G, kPaaThreads);
@@ -665,11 +667,11 @@ int launch_paa(Handle* h, int level, int n, long long nnz, const int* rowptr, co
               pass_of, b.agg_size, t, mode, b.slots, kMaxRoundSlots, h->ctrl};
     cudaMemsetAsync(b.slots, 0, sizeof(int) * kMaxRoundSlots, h->work);
     if (mode == UAAMG_PASS_MAXIMAL && n <= kPaaSmallN) {  // one block, state in shared memory
-        static bool attr_set = false;
+        static DevCache attr;
         const size_t smem = (sizeof(uint64_t) + 2) * (size_t)kPaaSmallN;
-        if (!attr_set) {
+        if (!attr.get(h->device)) {
             cudaFuncSetAttribute(k_paa_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr_set = true;
+            attr.set(h->device, 1);
         }
         k_paa_small<<<1, kPaaSmallThreads, smem, h->work>>>(a);
         count_launch(h);
@@ -688,13 +690,13 @@ int launch_paa(Handle* h, int level, int n, long long nnz, const int* rowptr, co
     const size_t blk_bytes = u16 ? paa_block_bytes<uint16_t>(n, nnz) : paa_block_bytes<int>(n, nnz);
     if (mode == UAAMG_PASS_SINGLE_ROUND && n <= kPaaBlockMaxN && blk_bytes <= kPaaBlockSmem) {
         // the whole level in one block's shared memory
-        static bool attr_set = false;
-        if (!attr_set) {
+        static DevCache attr;
+        if (!attr.get(h->device)) {
             cudaFuncSetAttribute(k_paa_sr_block<uint16_t>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPaaBlockSmem);
             cudaFuncSetAttribute(k_paa_sr_block<int>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPaaBlockSmem);
-            attr_set = true;
+            attr.set(h->device, 1);
         }
         if (u16)
             k_paa_sr_block<uint16_t><<<1, kPaaBlockThreads, blk_bytes, h->work>>>(a);
@@ -711,12 +713,14 @@ int launch_paa(Handle* h, int level, int n, long long nnz, const int* rowptr, co
         else if (avg <= 16) st = launch_paa_sr<16>(h, a, &grid);
         else st = launch_paa_sr<32>(h, a, &grid);
     } else {
-        static int blocks_per_sm = 0;
+        static DevCache occ;
+        int blocks_per_sm = occ.get(h->device);
         if (!blocks_per_sm) {
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_paa, kThreads, 0) !=
                     cudaSuccess ||
                 blocks_per_sm < 1)
                 blocks_per_sm = 1;
+            occ.set(h->device, blocks_per_sm);
         }
         int grid = blocks_per_sm * h->num_sms;
         const int need = grid_for(n, kThreads);
@@ -1077,12 +1081,14 @@ k_gj_inverse(int n, double* __restrict__ A, double* __restrict__ B, Ctrl* ctrl) 
 
 int launch_dense_coarsest(Handle* h, int n, const int* rowptr, const int* col,
                           const double* val, double* work, double* inv) {
-    static int blocks_per_sm = 0;
+    static DevCache occ;
+    int blocks_per_sm = occ.get(h->device);
     if (!blocks_per_sm) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_gj_inverse, kThreads,
                                                           0) != cudaSuccess ||
             blocks_per_sm < 1)
             blocks_per_sm = 1;
+        occ.set(h->device, blocks_per_sm);
     }
     cudaMemsetAsync(work, 0, sizeof(double) * (size_t)n * n, h->work);
     k_dense_gather<<<grid_for(n, kThreads), kThreads, 0, h->work>>>(n, rowptr, col, val, work);

@@ -192,19 +192,20 @@ __global__ void __launch_bounds__(kThreads) k_rowwarp_tma(RBArgs<T> a, Ctrl* ctr
 
 template <typename T, int MODE, int ND, int CAP>
 static int launch_one(Handle* h, const RBArgs<T>& a) {
-    static int grid_cache[64] = {0};
+    static DevCache grid_cache;  // persistent grid per device (the attribute is set with it)
     const size_t smem = sizeof(WarpStages<T, CAP>) * kTmaWarps;
-    const int dev = h->device < 64 ? h->device : 0;
-    if (!grid_cache[dev]) {
+    int full = grid_cache.get(h->device);
+    if (!full) {
         cudaFuncSetAttribute(k_rowwarp_tma<T, MODE, ND, CAP>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowwarp_tma<T, MODE, ND, CAP>,
                                                       kThreads, smem);
-        grid_cache[dev] = (per_sm > 0 ? per_sm : 1) * h->num_sms;
+        full = (per_sm > 0 ? per_sm : 1) * h->num_sms;
+        grid_cache.set(h->device, full);
     }
     const int nblk = grid_for((a.n + 31) / 32, kTmaWarps);
-    const int grid = nblk < grid_cache[dev] ? nblk : grid_cache[dev];
+    const int grid = nblk < full ? nblk : full;
     k_rowwarp_tma<T, MODE, ND, CAP><<<grid, kThreads, smem, h->work>>>(a, h->ctrl);
     count_launch(h);
     return check_cuda(cudaGetLastError());

@@ -42,7 +42,8 @@ static cudaMemPool_t pool_for(int dev) {
 
 void* dalloc_bytes(Handle* h, size_t bytes, int* status, bool temp) {
     if (*status != UAAMG_OK) return nullptr;
-    // at least 16 bytes of tail padding: bulk copies round their ranges up to 16 bytes
+    // at least 32 bytes of tail padding: bulk copies round their ranges up to 16-byte
+    // boundaries, which can reach 3 FP64 elements (24 bytes) past the end
     bytes = (bytes + 32 + 255) & ~(size_t)255;
     unsigned long long budget = g_budget.load();
     unsigned long long now = g_bytes.fetch_add(bytes) + bytes;
