@@ -91,7 +91,7 @@ typedef struct uaamg_params {
     int32_t tma_rows;     /* levels with at least this many rows run their SpMV-based kernels
                              as persistent blocks that stream the matrix into shared memory
                              with TMA bulk copies, one thread per row (0 = never); default
-                             262144.  Changes no vector entry; fused inner products are summed
+                             131072.  Changes no vector entry; fused inner products are summed
                              in another fixed order. */
     int32_t sell_rows;    /* levels (except the coarsest) with at least this many rows also
                              keep a sliced ELLPACK copy (slices of 32 rows, column-major;

@@ -106,7 +106,7 @@ void uaamg_default_params(uaamg_params* p) {
     p->kcycle_ratio = 0.0;
     p->min_coarsening = 0.0;
     p->jacobi_omega = 0.0;
-    p->tma_rows = 262144;
+    p->tma_rows = 131072;
     p->sell_rows = 0;
     p->fuse_below = 0;
 }
