@@ -1,6 +1,7 @@
 // kern_scan.cu -- exclusive prefix sum of int32 arrays (Blelloch-style, three launches:
-// tile sums, scan of the tile sums in one block, scan of each tile with its offset).  Used
-// for the ascending coarse numbering of Section 5.1 and for CSR row pointers.
+// tile sums, scan of the tile sums in one block, scan of each tile with its offset; one
+// launch for arrays of at most 16384 ints).  Used for the ascending coarse numbering of
+// Section 5.1 and for CSR row pointers.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -89,6 +90,33 @@ __global__ void __launch_bounds__(kThreads) k_scan_tiles(const int* __restrict__
     }
 }
 
+// Arrays of at most kScanSmallN ints in one launch: each of 1024 threads scans a contiguous
+// run of kScanSmallItems, and one block scan adds the runs' offsets.
+constexpr int kScanSmallItems = 16;
+constexpr int kScanSmallN = kScanTopThreads * kScanSmallItems;
+
+__global__ void __launch_bounds__(kScanTopThreads) k_scan_small(const int* __restrict__ in, int n,
+                                                               int* __restrict__ out,
+                                                               int* __restrict__ total) {
+    const int lo = min(n, (int)threadIdx.x * kScanSmallItems);
+    const int hi = min(n, lo + kScanSmallItems);
+    int v[kScanSmallItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanSmallItems; k++) {
+        v[k] = (lo + k < hi) ? in[lo + k] : 0;
+        s += v[k];
+    }
+    int tot;
+    int pre = block_exclusive_scan<kScanTopThreads>(s, &tot);
+#pragma unroll
+    for (int k = 0; k < kScanSmallItems; k++) {
+        if (lo + k < hi) out[lo + k] = pre;
+        pre += v[k];
+    }
+    if (threadIdx.x == 0 && total) *total = tot;
+}
+
 size_t scan_scratch_ints(long long n) { return (size_t)grid_for(n, kScanTile) + 1; }
 
 // out[i] = sum_{k<i} in[i]; *d_total = sum of all (device int, may be null).  `scratch`
@@ -96,6 +124,11 @@ size_t scan_scratch_ints(long long n) { return (size_t)grid_for(n, kScanTile) + 
 int scan_exclusive(Handle* h, const int* in, int* out, int n, int* d_total, int* scratch) {
     if (n <= 0) {
         if (d_total) cudaMemsetAsync(d_total, 0, sizeof(int), h->work);
+        return check_cuda(cudaGetLastError());
+    }
+    if (n <= kScanSmallN) {
+        k_scan_small<<<1, kScanTopThreads, 0, h->work>>>(in, n, out, d_total);
+        count_launch(h);
         return check_cuda(cudaGetLastError());
     }
     int nb = grid_for(n, kScanTile);
