@@ -104,11 +104,13 @@ int launch_priority(Handle* h, int n, const int* rowptr, const int* col, uint32_
 }
 
 // ---------------------------------------------------------------------------------------
-// Parallel aggregation, Algorithm 2: one persistent cooperative kernel runs every pass of
-// a level.  A pass is (A) rounds of coarse-vertex selection and (B) star aggregation.
+// Parallel aggregation, Algorithm 2: one kernel runs every pass of an aggregation.  A pass
+// is (A) rounds of coarse-vertex selection and (B) star aggregation.  Single-round mode
+// (the default) runs k_paa_sr<G> (cooperative, candidate worklists) or k_paa_sr_block (a
+// small level in one block's shared memory), below; maximal mode runs k_paa or k_paa_small.
 //
-// Round (two sweeps, separated by grid barriers; the state array is a snapshot per sweep,
-// so the result does not depend on thread order):
+// Round of maximal mode (two sweeps, separated by grid barriers; the state array is a
+// snapshot per sweep, so the result does not depend on thread order):
 //   sweep 1, every vertex v: b1[v] = max priority of the candidates in N[v] (closed
 //     neighbourhood), blocked[v] = N[v] contains a root of this pass;
 //   sweep 2, every candidate v: if some u in N[v] is blocked, v is within distance 2 of a
