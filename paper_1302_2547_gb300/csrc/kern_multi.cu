@@ -164,9 +164,19 @@ k_mrestrict(int nc, int R, const int* __restrict__ aggptr, const int* __restrict
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)nc * R) return;
     const int I = (int)(t / R), r = (int)(t % R);
+    const int q1 = aggptr[I + 1];
     T sum = T(0);
-    for (int q = aggptr[I]; q < aggptr[I + 1]; q++)
-        sum = add_rn(sum, s[(size_t)members[q] * R + r]);
+    for (int q = aggptr[I]; q < q1; q += 8) {  // members' loads issued together
+        int m[8];
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) m[u] = q + u < q1 ? members[q + u] : 0;
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = q + u < q1 ? s[(size_t)m[u] * R + r] : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (q + u < q1) sum = add_rn(sum, v[u]);
+    }
     rc[t] = sum;
 }
 

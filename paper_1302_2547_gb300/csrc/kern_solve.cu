@@ -185,6 +185,7 @@ template int launch_rowblock<double>(Handle*, int, int, const RBArgs<double>&);
 // ---------------------------------------------------------------------------------------
 // Restriction (Section 4.2): (P^T s)_I = sum of s over the members of aggregate I, one
 // thread per coarse entry, members in ascending order.
+constexpr int kRestrictBatch = 8;  // members whose loads a thread has in flight
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -195,8 +196,19 @@ k_restrict(int nc, const int* __restrict__ aggptr, const int* __restrict__ membe
     if (skip && *(volatile const int*)skip) return;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
+    const int q1 = aggptr[I + 1];
     T sum = T(0);
-    for (int q = aggptr[I]; q < aggptr[I + 1]; q++) sum = add_rn(sum, s[members[q]]);
+    for (int q = aggptr[I]; q < q1; q += kRestrictBatch) {  // members' loads issued together
+        int m[kRestrictBatch];
+        T v[kRestrictBatch];
+#pragma unroll
+        for (int u = 0; u < kRestrictBatch; u++) m[u] = q + u < q1 ? members[q + u] : 0;
+#pragma unroll
+        for (int u = 0; u < kRestrictBatch; u++) v[u] = q + u < q1 ? s[m[u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < kRestrictBatch; u++)
+            if (q + u < q1) sum = add_rn(sum, v[u]);
+    }
     rc[I] = sum;
 }
 
