@@ -818,16 +818,20 @@ int launch_coarse_m(Handle* h, int nc, const int* aggptr, const int* members,
     return check_cuda(cudaGetLastError());
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_coarse_build(int nc, const int* __restrict__ aggptr, const int* __restrict__ members,
-               const int* __restrict__ rowptr, const int* __restrict__ col,
-               const double* __restrict__ val, const int* __restrict__ agg,
-               const int* __restrict__ off, int* tJ, double* tV, int* sJ, double* sV,
-               int* __restrict__ cnt) {
-    const int lane = threadIdx.x & 31;
-    const int I = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (I >= nc) return;
-    const long long base = off[I];
+// Per coarse row, in one warp.  Rows whose members hold at most kCbMax entries run from
+// shared memory: the members' row bounds are read once, every entry's (agg[col], val) is
+// gathered with its loads in flight together, the stable rank sort reads the warp's keys
+// as shared-memory broadcasts, and each column's run is summed there.  Longer rows use the
+// same three steps through the global scratch buffers.  Both add every column's entries
+// from +0.0 in gather order (members ascending, then stored order) with rounded adds.
+constexpr int kCbMax = 128;
+constexpr int kCbWarps = kThreads / 32;
+
+__device__ void coarse_row_global(int I, int lane, const int* __restrict__ aggptr,
+                                  const int* __restrict__ members, const int* __restrict__ rowptr,
+                                  const int* __restrict__ col, const double* __restrict__ val,
+                                  const int* __restrict__ agg, long long base, int* tJ,
+                                  double* tV, int* sJ, double* sV, int* __restrict__ cnt) {
     // (1) gather
     int m = 0;
     for (int q = aggptr[I]; q < aggptr[I + 1]; q++) {
@@ -868,6 +872,104 @@ k_coarse_build(int nc, const int* __restrict__ aggptr, const int* __restrict__ m
             double sum = 0.0;
             for (int q = p; q < m && __ldcg(sJ + base + q) == J; q++)
                 sum = __dadd_rn(sum, __ldcg(sV + base + q));
+            tJ[base + idx] = J;
+            tV[base + idx] = sum;
+        }
+        seg += __popc(bal);
+    }
+    if (lane == 0) cnt[I] = seg;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_coarse_build(int nc, const int* __restrict__ aggptr, const int* __restrict__ members,
+               const int* __restrict__ rowptr, const int* __restrict__ col,
+               const double* __restrict__ val, const int* __restrict__ agg,
+               const int* __restrict__ off, int* tJ, double* tV, int* sJ, double* sV,
+               int* __restrict__ cnt) {
+    __shared__ int gj[kCbWarps][kCbMax], rj[kCbWarps][kCbMax];
+    __shared__ double gv[kCbWarps][kCbMax], rv[kCbWarps][kCbMax];
+    __shared__ int mk0[kCbWarps][32], moff[kCbWarps][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int I = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (I >= nc) return;  // whole warps leave together
+    const long long base = off[I];
+    const int q0 = aggptr[I], nm = aggptr[I + 1] - q0;
+    // row bounds of up to 32 members at once, and the entry offsets of their rows
+    int len = 0, k0 = 0;
+    if (nm <= 32 && lane < nm) {
+        const int s = members[q0 + lane];
+        k0 = rowptr[s];
+        len = rowptr[s + 1] - k0;
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int m = __shfl_sync(0xffffffffu, incl, 31);
+    if (nm > 32 || m > kCbMax) {
+        coarse_row_global(I, lane, aggptr, members, rowptr, col, val, agg, base, tJ, tV, sJ, sV,
+                          cnt);
+        return;
+    }
+    mk0[w][lane] = k0;
+    moff[w][lane + 1] = incl;
+    if (lane == 0) moff[w][0] = 0;
+    __syncwarp();
+    // (1) gather, all of a lane's entries in flight together
+    int ee[kCbMax / 32], cc[kCbMax / 32];
+    double vv[kCbMax / 32];
+#pragma unroll
+    for (int u = 0; u < kCbMax / 32; u++) {
+        const int e = lane + 32 * u;
+        ee[u] = -1;
+        if (e < m) {
+            int q = 0;
+            while (moff[w][q + 1] <= e) q++;  // the member holding entry e
+            const int k = mk0[w][q] + (e - moff[w][q]);
+            ee[u] = e;
+            cc[u] = col[k];
+            vv[u] = val[k];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kCbMax / 32; u++) {
+        if (ee[u] < 0) continue;
+        gj[w][ee[u]] = agg[cc[u]];
+        gv[w][ee[u]] = vv[u];
+    }
+    __syncwarp();
+    // (2) stable rank sort by coarse column
+#pragma unroll
+    for (int u = 0; u < kCbMax / 32; u++) {
+        const int e = lane + 32 * u;
+        if (e >= m) continue;
+        const int J = gj[w][e];
+        int rank = 0;
+        for (int f = 0; f < m; f++) {
+            const int Jf = gj[w][f];
+            rank += (Jf < J) || (Jf == J && f < e);
+        }
+        rj[w][rank] = J;
+        rv[w][rank] = gv[w][e];
+    }
+    __syncwarp();
+    // (3) one ordered sum per distinct column, written compacted
+    int seg = 0;
+    for (int p0 = 0; p0 < m; p0 += 32) {
+        const int p = p0 + lane;
+        bool start = false;
+        int J = 0;
+        if (p < m) {
+            J = rj[w][p];
+            start = (p == 0) || (rj[w][p - 1] != J);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, start);
+        if (start) {
+            const int idx = seg + __popc(bal & ((1u << lane) - 1u));
+            double sum = 0.0;
+            for (int q = p; q < m && rj[w][q] == J; q++) sum = __dadd_rn(sum, rv[w][q]);
             tJ[base + idx] = J;
             tV[base + idx] = sum;
         }
