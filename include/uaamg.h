@@ -78,7 +78,9 @@ typedef struct uaamg_params {
     double kcycle_tau;    /* > 0: skip the second step when |rho~| <= tau |rho|; default 0 */
     int32_t precision;    /* UAAMG_MIXED (default) or UAAMG_FP64 */
     int32_t max_iter;     /* outer iterations; default 200 */
-    int32_t use_graphs;   /* 1 (default): replay each outer iteration as a CUDA graph */
+    int32_t use_graphs;   /* 1 (default): run the outer iterations as one CUDA graph whose
+                             while node repeats an iteration until the device-side stopping
+                             test passes; 0: launch every kernel from the host */
     int32_t profile_class; /* UAAMG_KCLASS_* to time from setup on (0 = none, default) */
     int32_t agg_repeat;   /* 1 (default): one aggregation per level; 2: aggregate the coarse
                              graph once more before forming the level (Section 3.3) */
@@ -125,8 +127,10 @@ int uaamg_setup(const uaamg_csr* A, const uaamg_params* p, void* stream, uaamg_h
  * b[n] and x[n] are float64, host or device pointers (detected per call).  use_guess != 0
  * takes the initial x from x, else x0 = 0.  On return x holds the last iterate, *iters the
  * outer iteration count and *relres the final relative residual (both filled also for
- * UAAMG_ERR_NO_CONVERGENCE).  The call synchronises the handle's stream once per outer
- * iteration.
+ * UAAMG_ERR_NO_CONVERGENCE).  With use_graphs the iterations run on the device until the
+ * recursive residual passes the test, and the call synchronises the handle's stream a few
+ * times per solve (setup of the residual, that loop, the confirming FP64 residual); without
+ * it, or while a kernel class is profiled, it synchronises once per outer iteration.
  */
 int uaamg_solve(uaamg_handle* h, const double* b, double* x, double tol, int32_t use_guess,
                 int32_t* iters, double* relres);
@@ -177,7 +181,7 @@ typedef struct uaamg_stats {
     double setup_ms;      /* device time of the last setup (CUDA events) */
     double solve_ms;      /* device time of the last solve */
     int64_t launches;     /* kernels launched by this handle (graph nodes counted per replay) */
-    int64_t graph_nodes;  /* kernel nodes of one outer-iteration graph */
+    int64_t graph_nodes;  /* kernel nodes of one outer iteration in the last graph built */
     double opc;           /* operator complexity sum_l nnz_l / nnz_0 */
     double grid_complexity;
 } uaamg_stats;

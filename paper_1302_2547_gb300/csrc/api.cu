@@ -303,7 +303,7 @@ int uaamg_get_stats(const uaamg_handle* hh, uaamg_stats* s) {
     s->setup_ms = h->setup_ms;
     s->solve_ms = h->solve_ms;
     s->launches = h->launches;
-    s->graph_nodes = h->graph_nodes;
+    s->graph_nodes = h->loop_graph ? h->loop_nodes : h->graph_nodes;
     double z = 0, nn = 0;
     for (int l = 0; l < h->nlev; l++) {
         z += (double)h->lev[l].nnz;
