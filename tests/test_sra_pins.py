@@ -1,0 +1,363 @@
+"""Pins of the subgraph-reshaping oracle (Section 3.2, Algorithm 3, Eq. 3.8).
+
+None of these tests touches the GPU.  Each compares the oracle with something other than
+itself: the values the paper prints for Examples 3.2 and 3.3, Lemma 3.1, the identity
+|E v|^2 = |S v|^2 - |T v|^2, a brute-force operator norm by dense generalised eigenvalues,
+closed-form candidate counts, and brute-force searches over all splits.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import sra as SRA
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _laplacian(n, edges):
+    A = np.zeros((n, n))
+    for a, b, w in edges:
+        A[a, b] -= w
+        A[b, a] -= w
+    A[np.diag_indices(n)] = -A.sum(axis=1)
+    return A
+
+
+def _random_connected(n, extra, seed):
+    rng = np.random.default_rng(seed)
+    edges = {}
+    for k in range(1, n):
+        edges[(int(rng.integers(0, k)), k)] = float(np.exp(rng.standard_normal()))
+    for _ in range(extra):
+        a, b = sorted(int(x) for x in rng.integers(0, n, 2))
+        if a != b:
+            edges[(a, b)] = float(np.exp(rng.standard_normal()))
+    return _laplacian(n, [(a, b, w) for (a, b), w in edges.items()])
+
+
+def _basis_v(n):
+    """Orthonormal basis of V, the l2 complement of the constants."""
+    return sla.null_space(np.ones((1, n)))
+
+
+def _a_norm_sq_of_operator(A, X):
+    """sup_{v in V} |X v|_A^2 / |v|_A^2 by a dense generalised eigenproblem on V."""
+    B = _basis_v(A.shape[0])
+    H = B.T @ X.T @ A @ X @ B
+    G = B.T @ A @ B
+    return float(sla.eigh(0.5 * (H + H.T), G, eigvals_only=True)[-1])
+
+
+def _grid(nx, ny, wh, wv):
+    edges = []
+    for y in range(ny):
+        for x in range(nx):
+            i = x + nx * y
+            if x + 1 < nx:
+                edges.append((i, i + 1, wh))
+            if y + 1 < ny:
+                edges.append((i, i + nx, wv))
+    return _laplacian(nx * ny, edges)
+
+
+# ---------------------------------------------------------------------------------------
+# The energy |T(V_c)|_A^2 (Section 3.2, Eq. 3.8)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_energy_is_the_operator_norm_squared(seed):
+    n = 4 + seed
+    A = _random_connected(n, extra=n // 2, seed=seed)
+    R = SRA.l1_jacobi(A)
+    S_hat = np.eye(n) - R @ A
+    rng = np.random.default_rng(100 + seed)
+    for _ in range(3):
+        w = rng.standard_normal(n)
+        w -= w.mean()  # V_c must lie in V
+        T = SRA.a_projection(A, w) @ S_hat
+        brute = _a_norm_sq_of_operator(A, T)
+        assert SRA.t_energy(A, R, w) == pytest.approx(brute, rel=1e-9, abs=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_lemma_3_1_maximum_over_one_dimensional_spaces(seed):
+    # |S_V|_A = max over one-dimensional V_c of |T(V_c)|_A, attained by the top eigenvector
+    n = 5 + seed
+    A = _random_connected(n, extra=3, seed=20 + seed)
+    R = SRA.l1_jacobi(A)
+    S_hat = np.eye(n) - R @ A
+    B = _basis_v(n)
+    P = B @ B.T  # l2 projection onto V
+    S_V = P @ S_hat
+    top = _a_norm_sq_of_operator(A, S_V)
+    # S_V is A-self-adjoint on V: its A-norm is the largest |eigenvalue| of B^T A S_V B
+    # against B^T A B; the eigenvector spans the optimal coarse space
+    lam, Y = sla.eigh(B.T @ A @ S_V @ B, B.T @ A @ B)
+    k = int(np.argmax(np.abs(lam)))
+    w = B @ Y[:, k]
+    assert lam[k] ** 2 == pytest.approx(top, rel=1e-9)
+    assert SRA.t_energy(A, R, w) == pytest.approx(top, rel=1e-8)
+    rng = np.random.default_rng(seed)
+    for _ in range(5):
+        v = B @ rng.standard_normal(n - 1)
+        assert SRA.t_energy(A, R, v) <= top * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_energy_splits_the_smoother(seed):
+    # |E v|_A^2 = |S_V v|_A^2 - |T v|_A^2 for v in V, with E = (I - Q) S and T = Q S: this
+    # holds only when Q is the A-orthogonal projection
+    n = 7
+    A = _random_connected(n, extra=4, seed=40 + seed)
+    R = SRA.l1_jacobi(A)
+    S_hat = np.eye(n) - R @ A
+    B = _basis_v(n)
+    S_V = B @ B.T @ S_hat
+    w = SRA.psi_of(n, [0, 2, 5])
+    Q = SRA.a_projection(A, w)
+    rng = np.random.default_rng(seed)
+    for _ in range(4):
+        v = B @ rng.standard_normal(n - 1)
+        Ev = (np.eye(n) - Q) @ S_V @ v
+        Sv = S_V @ v
+        Tv = Q @ S_V @ v
+        assert Ev @ A @ Ev == pytest.approx(Sv @ A @ Sv - Tv @ A @ Tv, rel=1e-9, abs=1e-12)
+
+
+def test_energy_is_the_same_for_both_halves():
+    A = _random_connected(9, extra=5, seed=3)
+    R = SRA.l1_jacobi(A)
+    S = [0, 3, 4, 8]
+    Sc = [k for k in range(9) if k not in S]
+    e1 = SRA.t_energy(A, R, SRA.psi_of(9, S))
+    e2 = SRA.t_energy(A, R, SRA.psi_of(9, Sc))
+    assert e1 == pytest.approx(e2, rel=1e-10)
+
+
+def test_rank_one_trace_rule():
+    rng = np.random.default_rng(5)
+    u, v = rng.standard_normal(6), rng.standard_normal(6)
+    W = np.outer(u, v)
+    assert SRA.rank_one_trace(W) == pytest.approx(float(u @ v), rel=1e-12)
+    u[0] = 0.0  # W_00 = 0: the rule moves to the next diagonal entry
+    W = np.outer(u, v)
+    assert SRA.rank_one_trace(W) == pytest.approx(float(u @ v), rel=1e-12)
+
+
+def test_l1_jacobi_of_a_laplacian_is_half_the_inverse_diagonal():
+    A = _random_connected(6, extra=2, seed=9)
+    assert np.allclose(np.diag(SRA.l1_jacobi(A)), 0.5 / np.diag(A), rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------------------
+# The candidate splits (Algorithm 3 step 2): closed-form counts
+# ---------------------------------------------------------------------------------------
+
+def _path(n):
+    return _laplacian(n, [(k, k + 1, 1.0) for k in range(n - 1)])
+
+
+def _cycle(n):
+    return _laplacian(n, [(k, (k + 1) % n, 1.0) for k in range(n)])
+
+
+@pytest.mark.parametrize("n", range(2, 12))
+def test_candidate_counts_path_and_cycle(n):
+    # path: the prefix of length floor(n/2) (and, for odd n, also the suffix)
+    assert len(SRA.candidates(_path(n))) == (1 if n % 2 == 0 else 2)
+    if n >= 3:
+        # cycle: the arcs of length floor(n/2); for even n only those holding vertex 0
+        assert len(SRA.candidates(_cycle(n))) == (n // 2 if n % 2 == 0 else n)
+
+
+@pytest.mark.parametrize("n", range(2, 10))
+def test_candidate_counts_complete_and_star(n):
+    from math import comb
+
+    K = _laplacian(n, [(a, b, 1.0) for a in range(n) for b in range(a + 1, n)])
+    m = n // 2
+    assert len(SRA.candidates(K)) == (comb(n - 1, m - 1) if n % 2 == 0 else comb(n, m))
+    star = _laplacian(n, [(0, k, 1.0) for k in range(1, n)])
+    # a half without the centre is connected only if it is one leaf
+    expect = {2: 1, 3: 2}.get(n, 0)
+    assert len(SRA.candidates(star)) == expect
+
+
+def _connected_bf(A, S):
+    S = list(S)
+    seen, stack = {S[0]}, [S[0]]
+    while stack:
+        k = stack.pop()
+        for l in S:
+            if l not in seen and A[k, l] != 0.0:
+                seen.add(l)
+                stack.append(l)
+    return len(seen) == len(S)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_reshape_pair_maximises_over_all_splits(seed):
+    # brute force over every balanced split (itertools), energies from the dense operator norm
+    n = 6 + seed
+    A = _random_connected(n, extra=n, seed=60 + seed)
+    best_mask, energies = SRA.reshape_pair(A)
+    R = SRA.l1_jacobi(A)
+    S_hat = np.eye(n) - R @ A
+    found = {}
+    for S in itertools.combinations(range(n), n // 2):
+        Sc = [k for k in range(n) if k not in S]
+        if n % 2 == 0 and 0 not in S:
+            continue
+        if not (_connected_bf(A, S) and _connected_bf(A, Sc)):
+            continue
+        mask = sum(1 << k for k in S)
+        T = SRA.a_projection(A, SRA.psi_of(n, S)) @ S_hat
+        found[mask] = _a_norm_sq_of_operator(A, T)
+    assert set(found) == set(energies)
+    top = max(found.values())
+    assert found[best_mask] == pytest.approx(top, rel=1e-9)
+
+
+# ---------------------------------------------------------------------------------------
+# Examples 3.2 and 3.3: the values the paper prints after Algorithm 3
+# ---------------------------------------------------------------------------------------
+
+def _golden_examples():
+    rows = []
+    with open(os.path.join(GOLDEN, "sra_examples.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, wh, wv, q2, e = line.split()
+            rows.append((name, float(wh), float(wv), float(q2), float(e)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_examples(), ids=lambda r: r[0])
+def test_examples_3_2_and_3_3_energy_of_the_l2_projection(row):
+    name, wh, wv, q2_paper, _e_paper = row
+    A = _grid(4, 4, wh, wv)
+    mask, _ = SRA.reshape_pair(A)
+    S = [k for k in range(16) if mask >> k & 1]
+    psi = SRA.psi_of(16, S)
+    Q_l2 = np.outer(psi, psi) / float(psi @ psi)
+    q2 = _a_norm_sq_of_operator(A, Q_l2)
+    assert round(q2, 2) == q2_paper
+    if wv > wh:
+        # anisotropic: the aggregates follow the strong (vertical) couplings, whole columns
+        cols = {k % 4 for k in S}
+        assert len(cols) == 2 and all(x + 4 * y in S for x in cols for y in range(4))
+
+
+def test_examples_value_is_discriminating():
+    # of the 70 balanced connected splits of the 4 x 4 grid, only the two straight halvings
+    # have |Q|_A^2 = 1.50, so the printed value fixes the split up to symmetry
+    A = _grid(4, 4, 1.0, 1.0)
+    hits = 0
+    for mask in SRA.candidates(A):
+        psi = SRA.psi_of(16, [k for k in range(16) if mask >> k & 1])
+        q2 = _a_norm_sq_of_operator(A, np.outer(psi, psi) / float(psi @ psi))
+        hits += round(q2, 2) == 1.50
+    assert len(SRA.candidates(A)) == 70 and hits == 2
+
+
+# ---------------------------------------------------------------------------------------
+# A level: the matching and the rounds
+# ---------------------------------------------------------------------------------------
+
+def test_fmix32_matches_the_c_oracle(oracle):
+    xs = np.random.default_rng(1).integers(0, 2**32, 200, dtype=np.uint64).astype(np.uint32)
+    got = SRA.fmix32(xs)
+    for x, g in zip(xs, got):
+        assert int(g) == oracle.fmix32(int(x))
+
+
+def _matching_bf(csr, agg, nc, salt):
+    """Pure-Python statement of the matching, edge by edge."""
+    size = [0] * nc
+    for a in agg:
+        size[a] += 1
+    best = {}
+    for s in range(csr.n):
+        for q in range(csr.rowptr[s], csr.rowptr[s + 1]):
+            t = int(csr.col[q])
+            I, J = int(agg[s]), int(agg[t])
+            if I == J or csr.val[q] == 0.0 or size[I] + size[J] > SRA.UNION_MAX:
+                continue
+            lo, hi = min(I, J), max(I, J)
+            w = int(SRA.pair_weight(np.uint32(lo), np.uint32(hi), salt))
+            key = (w, -J)
+            if I not in best or key > best[I]:
+                best[I] = key
+    partner = {I: -k[1] for I, k in best.items()}
+    return sorted((I, J) for I, J in partner.items() if I < J and partner.get(J) == I)
+
+
+def _level0_aggregation(oracle, csr, t=5, seed=0x5EED):
+    P = oracle.priorities(csr.rowptr, csr.col, seed, 0)
+    root_of, _, _ = oracle.paa(csr.rowptr, csr.col, P, t, oracle.SINGLE_ROUND)
+    return oracle.renumber(root_of)
+
+
+@pytest.mark.parametrize("case", ["grid", "random", "dense_unbounded"])
+def test_matching_matches_brute_force(oracle, inputs, case):
+    if case == "grid":
+        csr, t = inputs.grid2d(12, 10), 5
+    elif case == "random":
+        csr, t = inputs.random_graph(150, 120, seed=4), 5
+    else:  # large aggregates (t = 0): many neighbouring pairs exceed the union cap
+        csr, t = inputs.random_graph(200, 1500, seed=6), 0
+    agg, nc = _level0_aggregation(oracle, csr, t=t)
+    if case == "dense_unbounded":
+        size = np.bincount(agg, minlength=nc)
+        assert size.max() * 2 > SRA.UNION_MAX
+    for r in range(3):
+        salt = SRA.round_salt(0x5EED, 0, r)
+        pairs = SRA.matching(csr.rowptr, csr.col, csr.val, agg, nc, salt)
+        assert pairs == _matching_bf(csr, agg, nc, salt)
+        flat = [x for p in pairs for x in p]
+        assert len(flat) == len(set(flat))  # disjoint
+        assert len(pairs) > 0
+
+
+@pytest.mark.parametrize("case", ["grid", "grid3d_weighted", "random"])
+def test_round_invariants(oracle, inputs, case):
+    csr = {"grid": lambda: inputs.grid2d(14, 12),
+           "grid3d_weighted": lambda: inputs.grid3d(6, 5, 4, sigma=0.25, seed=2),
+           "random": lambda: inputs.random_graph(160, 100, seed=8, integer_weights=False)}[case]()
+    agg, nc = _level0_aggregation(oracle, csr)
+    rec = []
+    new = SRA.reshape_round(csr.rowptr, csr.col, csr.val, agg, nc, 0x5EED, 0, 0, record=rec)
+    assert new.min() == 0 and new.max() == nc - 1
+    assert len(np.unique(new)) == nc  # Algorithm 3 keeps the number of aggregates
+    A = csr.dense()
+    touched = set()
+    for I, J, U, best, _ in rec:
+        touched.update(U.tolist())
+        assert set(np.flatnonzero((agg == I) | (agg == J))) == set(U.tolist())
+        if best is None:
+            assert np.array_equal(new[U], agg[U])
+            continue
+        a = [u for u in U if new[u] == I]
+        b = [u for u in U if new[u] == J]
+        assert len(a) + len(b) == len(U) and abs(len(a) - len(b)) <= 1
+        assert min(U) in a  # the half holding the smallest vertex keeps the smaller number
+        Asub = A[np.ix_(U, U)]
+        pos = {u: k for k, u in enumerate(U)}
+        assert _connected_bf(Asub, [pos[u] for u in a]) and _connected_bf(Asub, [pos[u] for u in b])
+    untouched = np.setdiff1d(np.arange(csr.n), np.array(sorted(touched), dtype=np.int64))
+    assert np.array_equal(new[untouched], agg[untouched])
+    assert len(rec) > 0 and any(r[3] is not None for r in rec)
+
+
+def test_local_laplacian_of_a_subgraph(inputs):
+    csr = inputs.grid2d(5, 4, dirichlet=True)
+    U = np.array([1, 2, 6, 7, 12])
+    A_hat = SRA.local_laplacian(csr.rowptr, csr.col, csr.val, U)
+    A = csr.dense()[np.ix_(U, U)]
+    off = A - np.diag(np.diag(A))
+    assert np.array_equal(A_hat - np.diag(np.diag(A_hat)), off)
+    assert np.allclose(A_hat.sum(axis=1), 0.0, atol=0)  # Neumann: the Dirichlet part drops
