@@ -405,6 +405,60 @@ def run_rgg(steps=3, warmup=1):
             "relres_host_fp64": float(np.linalg.norm(bb - Asp @ xb) / np.linalg.norm(bb))}
 
 
+# FP64 peak of GB300 for ALU-bound kernels: 152 SMs x 2 FP64 FMA per clock x 2 operations
+# x the maximum SM clock (2070 MHz).  Adds and multiplies count one operation, an FMA two.
+FP64_SMS, FP64_FMA_PER_CLK, FP64_MAX_MHZ = 152, 2, 2070.0
+
+
+def run_sra(rounds=2, steps=3, warmup=1):
+    """Subgraph reshaping (Algorithm 3) of every level's first aggregation stage on the
+    headline workload: setup with `rounds` rounds, the pair kernel timed by CUDA events on the
+    setup stream and its FP64 operations counted by the kernel itself, then one solve."""
+    import torch
+
+    from paper_1302_2547_gb300 import _lib as U
+
+    A, b = workload()
+    dev = torch.device("cuda:0")
+    rp, cc, vv = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    p = bench_params(U, U.UAAMG_MIXED, U.UAAMG_KCLASS_SRA)
+    p.sra_rounds = rounds
+    rec = []
+    for k in range(warmup + steps):
+        xd.zero_()
+        h = U.uaamg_setup(rp, cc, vv, p)
+        try:
+            prof = U.uaamg_get_profile(h)
+            U.uaamg_set_profiling(h, 0)  # the solve runs its device-side loop, untimed
+            st, it, rr = U.uaamg_solve(h, bd, xd, TOL)
+            if st != 0:
+                raise RuntimeError(f"solve status {st} after {it} iterations")
+            s = U.uaamg_get_stats(h)
+        finally:
+            U.uaamg_free(h)
+        if k >= warmup:
+            rec.append((prof, s, it))
+    launches = sum(r[0][0] for r in rec)
+    ms = sum(r[0][1] for r in rec)
+    ops = float(np.median([r[0][2] for r in rec]))
+    avg_s = ms / launches / 1000.0
+    achieved = ops / avg_s / 1e9
+    peak = FP64_SMS * FP64_FMA_PER_CLK * 2 * FP64_MAX_MHZ / 1000.0
+    return {"rounds": rounds, "levels": "first aggregation stage of every level",
+            "setup_ms": round(float(np.median([r[1]["setup_ms"] for r in rec])), 3),
+            "solve_ms": round(float(np.median([r[1]["solve_ms"] for r in rec])), 3),
+            "iterations": int(np.median([r[2] for r in rec])),
+            "pair_kernel_level0": {
+                "launches_timed": launches, "avg_launch_us": round(avg_s * 1e6, 2),
+                "fp64_ops_per_launch": ops,
+                "roofline": {"bound": "alu", "achieved": round(achieved, 1), "peak": peak,
+                             "unit": "GFLOP/s", "frac": round(achieved / peak, 4),
+                             "traffic": None,
+                             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"}}}
+
+
 def run_serving(n_requests=120, seed=2024):
     """The solve service (uaamg_server_*) under a Poisson stream of requests, shaped like the
     serving workload with smaller sizes so that it runs in seconds: 12 matrices (2D grid, 3D
@@ -519,6 +573,10 @@ def main():
     ap.add_argument("--skip-batched", action="store_true", help="do not time solve_many")
     ap.add_argument("--skip-serving", action="store_true",
                     help="do not run the solve service under a request stream")
+    ap.add_argument("--skip-sra", action="store_true",
+                    help="do not time subgraph reshaping (Algorithm 3) on the workload")
+    ap.add_argument("--sra-only", action="store_true",
+                    help="print only the subgraph-reshaping measurement as one JSON line")
     ap.add_argument("--rgg", action="store_true",
                     help="also time the 4M-point random geometric graph (about a minute)")
     ap.add_argument("--tma-rows", type=int, default=None,
@@ -569,8 +627,17 @@ def main():
         import torch.distributed as dist
 
         dist.barrier()
+    if args.sra_only:
+        if rank == 0:
+            print(json.dumps({"workload": WORKLOAD, "sra": run_sra()}))
+        return
     out = run_gpu(args, rank, world)
     if rank == 0:
+        if world == 1 and not args.skip_sra:
+            try:
+                out["sra"] = run_sra()
+            except Exception as e:  # reported, not hidden: the main line still stands
+                out["sra"] = {"error": f"{type(e).__name__}: {e}"}
         if world == 1 and args.rgg:
             out["rgg_4m"] = run_rgg()
         if world == 1 and not args.skip_serving:

@@ -103,6 +103,17 @@ typedef struct uaamg_params {
     int32_t fuse_below;   /* coarse levels with at most this many unknowns run their K-cycle
                              in one fused single-block kernel (pre = post = 1 only); 0 = off
                              (default: on GB300 one block is slower than launching) */
+    int32_t sra_rounds;   /* 0 (default) .. 64: rounds of subgraph reshaping (Section 3.2,
+                             Algorithm 3) applied to each level's aggregation before its coarse
+                             operator is formed (the first stage when agg_repeat = 2).  A round
+                             matches neighbouring aggregates in pairs whose union has at most 16
+                             vertices (mutual choice of a seeded hashed pair weight) and splits
+                             every pair's union into the two connected halves of sizes
+                             floor(n/2) and ceil(n/2) that maximise |T(V_c)|_A^2 on the union's
+                             local graph Laplacian (l1-Jacobi smoother).  Energies within a
+                             relative 1e-9 count as equal (the split whose mask of the union's
+                             ascending vertices is smallest wins).  A pair without such a split
+                             stays as it is.  The number of aggregates does not change. */
 } uaamg_params;
 
 typedef struct uaamg_handle uaamg_handle;
@@ -197,8 +208,11 @@ int uaamg_get_stats(const uaamg_handle* h, uaamg_stats* s);
 #define UAAMG_KCLASS_SPMV64 2   /* level-0 FP64 SpMV + dot kernel of the outer iteration */
 #define UAAMG_KCLASS_PAA 3      /* the aggregation kernel of setup level 0 */
 #define UAAMG_KCLASS_COARSE 4   /* the coarse-operator assembly kernel of setup level 0 */
+#define UAAMG_KCLASS_SRA 5      /* the pair kernel of subgraph reshaping on setup level 0; its
+                                   "bytes" per launch are FP64 operations per launch */
 int uaamg_set_profiling(uaamg_handle* h, int32_t kclass);
-/* launches, total ms, and algorithmic bytes moved per launch of the profiled class */
+/* launches, total ms, and algorithmic bytes moved per launch of the profiled class (for
+ * UAAMG_KCLASS_SRA: algorithmic FP64 operations per launch, counted by the kernel) */
 int uaamg_get_profile(const uaamg_handle* h, int64_t* launches, double* total_ms,
                       double* bytes_per_launch);
 

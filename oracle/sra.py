@@ -28,8 +28,10 @@ Readings where the paper is silent, ambiguous or garbled:
 * The paper states that the trace equals |T|_A.  It is |T|_A squared.  The argmax is the
   same.
 * Each unordered split is a candidate once.  For an even n, S is the half that holds local
-  vertex 0.  A candidate also needs a positive cut 1_S^T A_hat 1_S.  Among exactly equal
-  energies, the smallest mask sum_{k in S} 2^k wins.  The half holding local vertex 0 keeps
+  vertex 0.  A candidate also needs a positive cut 1_S^T A_hat 1_S.  Symmetric splits have
+  mathematically equal energies that FP64 rounds apart.  So energies within a relative
+  TIE_REL count as equal: scanning the masks sum_{k in S} 2^k in ascending order, a
+  candidate replaces the best one only when its energy exceeds it by more than that.  The half holding local vertex 0 keeps
   the smaller of the two aggregate numbers.  A pair without a candidate stays unchanged.
 * The paper traverses the pairs of neighbouring aggregates without fixing an order.  Here a
   level is reshaped in rounds, and each round reshapes the pairs of a matching at once:
@@ -47,6 +49,7 @@ from __future__ import annotations
 import numpy as np
 
 UNION_MAX = 16
+TIE_REL = 1e-9
 _M32 = 0xFFFFFFFF
 
 
@@ -195,7 +198,7 @@ def reshape_pair(A_hat):
         return None, {}
     best = None
     for mask in sorted(energies):
-        if best is None or energies[mask] > energies[best]:
+        if best is None or energies[mask] > energies[best] + TIE_REL * abs(energies[best]):
             best = mask
     return best, energies
 

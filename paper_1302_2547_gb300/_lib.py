@@ -17,6 +17,7 @@ UAAMG_ERR_NO_CONVERGENCE = 4
 UAAMG_FP64, UAAMG_MIXED = 0, 1
 UAAMG_PASS_MAXIMAL, UAAMG_PASS_SINGLE_ROUND = 0, 1
 UAAMG_KCLASS_SMOOTH0, UAAMG_KCLASS_SPMV64, UAAMG_KCLASS_PAA, UAAMG_KCLASS_COARSE = 1, 2, 3, 4
+UAAMG_KCLASS_SRA = 5
 
 # every symbol declared in include/uaamg.h
 EXPORTS = [
@@ -44,7 +45,8 @@ class uaamg_params(C.Structure):
                 ("use_graphs", C.c_int32), ("profile_class", C.c_int32),
                 ("agg_repeat", C.c_int32), ("kcycle_ratio", C.c_double),
                 ("min_coarsening", C.c_double), ("jacobi_omega", C.c_double),
-                ("tma_rows", C.c_int32), ("sell_rows", C.c_int32), ("fuse_below", C.c_int32)]
+                ("tma_rows", C.c_int32), ("sell_rows", C.c_int32), ("fuse_below", C.c_int32),
+                ("sra_rounds", C.c_int32)]
 
 
 class uaamg_stats(C.Structure):

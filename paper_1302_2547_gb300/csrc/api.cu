@@ -74,10 +74,10 @@ static bool params_ok(const uaamg_params* p) {
            p->pre >= 0 && p->pre <= 8 && p->post >= 0 && p->post <= 8 &&
            (p->kcycle_inner == 1 || p->kcycle_inner == 2) && p->kcycle_tau >= 0.0 &&
            (p->precision == UAAMG_FP64 || p->precision == UAAMG_MIXED) && p->max_iter >= 0 &&
-           p->profile_class >= 0 && p->profile_class <= UAAMG_KCLASS_COARSE &&
+           p->profile_class >= 0 && p->profile_class <= UAAMG_KCLASS_SRA &&
            (p->agg_repeat == 1 || p->agg_repeat == 2) && p->kcycle_ratio >= 0.0 &&
            p->min_coarsening >= 0.0 && p->fuse_below >= 0 && p->jacobi_omega >= 0.0 &&
-           p->tma_rows >= 0 && p->sell_rows >= 0;
+           p->tma_rows >= 0 && p->sell_rows >= 0 && p->sra_rounds >= 0 && p->sra_rounds <= 64;
 }
 
 }  // namespace uaamg
@@ -109,6 +109,7 @@ void uaamg_default_params(uaamg_params* p) {
     p->tma_rows = 131072;
     p->sell_rows = 0;
     p->fuse_below = 0;
+    p->sra_rounds = 0;
 }
 
 int uaamg_setup(const uaamg_csr* A, const uaamg_params* p, void* stream, uaamg_handle** out) {
@@ -316,7 +317,7 @@ int uaamg_get_stats(const uaamg_handle* hh, uaamg_stats* s) {
 
 int uaamg_set_profiling(uaamg_handle* hh, int32_t kclass) {
     Handle* h = reinterpret_cast<Handle*>(hh);
-    if (!h || kclass < 0 || kclass > UAAMG_KCLASS_COARSE) return UAAMG_ERR_INVALID_ARG;
+    if (!h || kclass < 0 || kclass > UAAMG_KCLASS_SRA) return UAAMG_ERR_INVALID_ARG;
     h->prof_class = kclass;
     h->prof_launches = 0;
     h->prof_ms = 0.0;

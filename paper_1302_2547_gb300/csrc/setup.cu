@@ -172,6 +172,11 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
                 goto done;
             F.passes = a1.passes;
             if (a1.nc >= F.n) break;  // no coarsening possible: F is the coarsest level
+            // subgraph reshaping of the aggregates (Section 3.2, Algorithm 3)
+            if (h->p.sra_rounds > 0 &&
+                (st = reshape_aggregation(h, l, G.n, G.rowptr, G.col, G.val, a1.nc, a1.agg,
+                                          &a1.aggptr, &a1.members, S.scan_tmp)))
+                goto done;
             Csr C1;
             if ((st = assemble(h, l, G, a1, S, hb, &C1))) goto done;
             Agg fin = a1;

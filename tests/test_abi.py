@@ -50,6 +50,7 @@ def test_default_params_and_status_strings(built):
     p = U.uaamg_default_params()
     assert (p.coarse_size, p.max_levels, p.max_agg_size, p.pass_mode) == (64, 25, 5, 1)
     assert (p.pre, p.post, p.kcycle_inner, p.precision, p.max_iter) == (1, 1, 2, 1, 200)
+    assert p.sra_rounds == 0
     assert U.status_string(0) == "ok" and "CSR" in U.status_string(2)
 
 
@@ -59,7 +60,8 @@ def test_params_are_checked_before_any_device_work(built):
 
     A = I.grid2d(8)
     for bad in ({"max_agg_size": 1}, {"kcycle_inner": 3}, {"precision": 7},
-                {"max_levels": 0}, {"pass_mode": 4}, {"pre": -1}):
+                {"max_levels": 0}, {"pass_mode": 4}, {"pre": -1}, {"sra_rounds": -1},
+                {"sra_rounds": 65}, {"profile_class": 6}):
         with pytest.raises(U.UaamgError) as e:
             U.uaamg_setup(A.rowptr, A.col, A.val, U.uaamg_default_params(**bad))
         assert e.value.status == 1
