@@ -5,10 +5,10 @@
 //   k_sra_propose  per fine row: propose to the eligible neighbouring aggregate of largest
 //                  pair weight (64-bit atomicMax on (weight, ~J))
 //   k_sra_match    mutual proposals = the round's pairs, appended to a list
-//   k_sra_pairs    persistent warps, one pair at a time: the union's local graph Laplacian
-//                  (a small CSR in shared memory), every balanced split with both halves
-//                  connected (Algorithm 3 step 2), the split of largest energy (step 3), the
-//                  new aggregate numbers
+//   k_sra_pairs    persistent half-warps, one pair at a time each: the union's local graph
+//                  Laplacian (a small CSR in shared memory), every balanced split with both
+//                  halves connected (Algorithm 3 step 2), the split of largest energy
+//                  (step 3), the new aggregate numbers
 //   scan           new sizes -> new aggregate offsets
 //   k_sra_members  per aggregate: its member list, ascending (unchanged ones are copied)
 //
@@ -18,16 +18,17 @@
 // psi = (1/|S| + 1/|S^c|) 1_S modulo the constants, and the trace reduces to
 //     J(S) = (c - 2 g^T R g + h^T A h) / c,   g = A 1_S,  h = R g,  c = 1_S^T A 1_S,
 // which needs no pseudo-inverse.  A is a graph Laplacian, so g lives on the cut edges and
-// h^T A h is the sum over the edges of w_kl (h_k - h_l)^2.  FP64 throughout.  Each lane enumerates a contiguous range
-// of candidate masks in ascending order (colex ranks), and the warp keeps the largest J.
-// Energies within a relative kSraTie count as equal, and the smallest mask among them wins
-// (symmetric splits have equal energies up to rounding).
+// h^T A h is the sum over the edges of w_kl (h_k - h_l)^2.  FP64 throughout.  Each lane of
+// a pair's group enumerates a contiguous range of candidate masks in ascending order (colex
+// ranks), and the group keeps the largest J.  Energies within a relative kSraTie count as
+// equal, and the smallest mask among them wins (symmetric splits have equal energies up to
+// rounding).
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace uaamg {
 
-constexpr int kSraWarps = 4;  // warps per block of k_sra_pairs (one pair at a time each)
+constexpr int kSraWarps = 4;  // warps per block of k_sra_pairs
 constexpr double kSraTie = 1e-9;
 
 __device__ __forceinline__ uint32_t sra_fmix32(uint32_t h) {
@@ -146,10 +147,12 @@ __device__ __forceinline__ bool sra_connected(uint32_t X, const uint32_t (&adj)[
 
 constexpr int kSraMaxNb = kSraUnionMax * (kSraUnionMax - 1);  // directed local edges
 
-struct SraWarpSmem {
+constexpr int kSraGroup = 16;  // lanes per pair: each warp reshapes two pairs at a time
+
+struct SraGroupSmem {
     union {
         double A[kSraUnionMax * kSraUnionMax];  // the local matrix, while it is built
-        double h[kSraUnionMax * 32];            // then h = R A 1_S, one column per lane
+        double h[kSraUnionMax * kSraGroup];     // then h = R A 1_S, one column per lane
     };
     double w[kSraMaxNb];  // local graph as CSR: w = -a_kl of each neighbour
     double r[kSraUnionMax];
@@ -166,37 +169,41 @@ k_sra_pairs(const int* __restrict__ list, const int* __restrict__ count,
             const int* __restrict__ members, const unsigned long long* __restrict__ prop,
             int* __restrict__ agg, int* __restrict__ newsize, int* __restrict__ pair_of,
             unsigned long long* __restrict__ flops) {
-    __shared__ SraWarpSmem sm_all[kSraWarps];
+    __shared__ SraGroupSmem sm_all[kSraWarps * 2];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    SraWarpSmem& sm = sm_all[wib];
+    const int grp = threadIdx.x / kSraGroup;     // group within the block
+    const int gl = lane & (kSraGroup - 1);       // lane within the group
+    const uint32_t gmask = 0xFFFFu << (lane & kSraGroup);
+    SraGroupSmem& sm = sm_all[grp];
     const int npairs = *count;
-    const int nwarps = gridDim.x * kSraWarps;
+    const int ngroups = gridDim.x * kSraWarps * 2;
     unsigned long long ops = 0ull;
-    for (int pw = blockIdx.x * kSraWarps + wib; pw < npairs; pw += nwarps) {
+    for (int pw = blockIdx.x * kSraWarps * 2 + grp; pw < npairs; pw += ngroups) {
         const int I = list[pw];
         const int J = sra_partner(prop[I]);
         const int oI = aggptr[I], a = aggptr[I + 1] - oI;
         const int oJ = aggptr[J], b = aggptr[J + 1] - oJ;
         const int nu = a + b;
         if (nu < 2 || nu > kSraUnionMax) continue;  // eligible pairs never are
-        __syncwarp();  // the previous pair's shared data is no longer read
+        __syncwarp(gmask);  // the previous pair's shared data is no longer read
 
         // (1) the union, sorted ascending (the two member lists are disjoint)
         int v = 0x7FFFFFFF;
-        if (lane < a) v = members[oI + lane];
-        else if (lane < nu) v = members[oJ + lane - a];
+        if (gl < a) v = members[oI + gl];
+        else if (gl < nu) v = members[oJ + gl - a];
         int rank = 0;
-        for (int e = 0; e < nu; e++) rank += (__shfl_sync(0xffffffffu, v, e) < v) ? 1 : 0;
-        if (lane < nu) sm.u[rank] = v;
-        for (int e = lane; e < kSraUnionMax * kSraUnionMax; e += 32) sm.A[e] = 0.0;
-        __syncwarp();
+        for (int e = 0; e < nu; e++)
+            rank += (__shfl_sync(gmask, v, e, kSraGroup) < v) ? 1 : 0;
+        if (gl < nu) sm.u[rank] = v;
+        for (int e = gl; e < kSraUnionMax * kSraUnionMax; e += kSraGroup) sm.A[e] = 0.0;
+        __syncwarp(gmask);
 
         // (2) the union's local graph Laplacian: off-diagonal entries of the induced
-        // subgraph, diagonal = minus their row sum (ascending l); l1-Jacobi weight
-        // 1 / (a_kk + sum |a_kl|); neighbours are the non-zero off-diagonal entries
-        if (lane < nu) {
-            const int s = sm.u[lane];
+        // subgraph (neighbours: the non-zero ones), diagonal = minus their row sum
+        // (ascending l); l1-Jacobi weight 1 / (a_kk + sum |a_kl|)
+        uint32_t nbm = 0u;
+        if (gl < nu) {
+            const int s = sm.u[gl];
             for (int q = rowptr[s]; q < rowptr[s + 1]; q++) {
                 const int t = col[q];
                 if (t == s) continue;
@@ -205,49 +212,45 @@ k_sra_pairs(const int* __restrict__ list, const int* __restrict__ count,
                     const int mid = (lo + hi) >> 1;
                     const int x = sm.u[mid];
                     if (x == t) {
-                        sm.A[lane * kSraUnionMax + mid] = val[q];
+                        const double vq = val[q];
+                        sm.A[gl * kSraUnionMax + mid] = vq;
+                        if (vq != 0.0) nbm |= 1u << mid;
                         break;
                     }
                     if (x < t) lo = mid + 1;
                     else hi = mid - 1;
                 }
             }
-        }
-        __syncwarp();
-        uint32_t nbm = 0u;
-        if (lane < nu) {
             double d = 0.0, absum = 0.0;
-            for (int l = 0; l < nu; l++) {
-                if (l == lane) continue;
-                const double x = sm.A[lane * kSraUnionMax + l];
+            for (uint32_t bits = nbm; bits; bits &= bits - 1u) {
+                const double x = sm.A[gl * kSraUnionMax + (__ffs(bits) - 1)];
                 d = __dadd_rn(d, x);
                 absum = __dadd_rn(absum, fabs(x));
-                if (x != 0.0) nbm |= 1u << l;
             }
             const double m = __dadd_rn(-d, absum);
-            sm.r[lane] = (m != 0.0) ? 1.0 / m : 0.0;
-            sm.adj[lane] = nbm;
+            sm.r[gl] = (m != 0.0) ? 1.0 / m : 0.0;
+            sm.adj[gl] = nbm;
         }
-        // neighbour lists (local CSR), offsets by a warp prefix sum of the degrees
+        // neighbour lists (local CSR), offsets by a group prefix sum of the degrees
         const int deg = __popc(nbm);
         int off = deg;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, off, o);
-            if (lane >= o) off += y;
+        for (int o = 1; o < kSraGroup; o <<= 1) {
+            const int y = __shfl_up_sync(gmask, off, o, kSraGroup);
+            if (gl >= o) off += y;
         }
         off -= deg;
-        if (lane < nu) {
+        if (gl < nu) {
             int e = off;
             for (uint32_t bits = nbm; bits; bits &= bits - 1u) {
                 const int l = __ffs(bits) - 1;
                 sm.nb[e] = (uint8_t)l;
-                sm.w[e] = -sm.A[lane * kSraUnionMax + l];
+                sm.w[e] = -sm.A[gl * kSraUnionMax + l];
                 e++;
             }
-            sm.ptr[lane] = (uint8_t)off;
-            if (lane == nu - 1) sm.ptr[nu] = (uint8_t)(off + deg);
+            sm.ptr[gl] = (uint8_t)off;
+            if (gl == nu - 1) sm.ptr[nu] = (uint8_t)(off + deg);
         }
-        __syncwarp();  // sm.A is dead from here on: its space holds h
+        __syncwarp(gmask);  // sm.A is dead from here on: its space holds h
         uint32_t adj[kSraUnionMax];
         int edges2 = 0;  // directed local edges = twice the undirected ones
 #pragma unroll
@@ -263,8 +266,8 @@ k_sra_pairs(const int* __restrict__ list, const int* __restrict__ count,
         const int N = even ? nu - 1 : nu;
         const int K = even ? m - 1 : m;
         const uint32_t total = kSraBinom.v[N][K];
-        const uint32_t per = (total + 31u) / 32u;
-        const uint32_t r0 = (uint32_t)lane * per;
+        const uint32_t per = (total + kSraGroup - 1u) / kSraGroup;
+        const uint32_t r0 = (uint32_t)gl * per;
         const uint32_t r1 = min(total, r0 + per);
         const uint32_t full = (1u << nu) - 1u;
         double bn = -1.0, bc = 1.0;  // best energy as the fraction bn / bc
@@ -280,7 +283,7 @@ k_sra_pairs(const int* __restrict__ list, const int* __restrict__ count,
                 rem -= kSraBinom.v[c][i];
             }
         }
-        double* hcol = sm.h + lane;  // h_k of this lane's candidate at hcol[32 k]
+        double* hcol = sm.h + gl;  // h_k of this lane's candidate at hcol[kSraGroup k]
         for (uint32_t rk = r0; rk < r1; rk++) {
             const uint32_t S = even ? ((x << 1) | 1u) : x;
             if (K > 0 && rk + 1 < r1) {  // next K-subset in colex order (Gosper's rule)
@@ -302,17 +305,17 @@ k_sra_pairs(const int* __restrict__ list, const int* __restrict__ count,
                     g += (sk == sl) ? 0.0 : (sk ? we : -we);
                 }
                 const double hk = g * sm.r[k];
-                hcol[32 * k] = hk;
+                hcol[kSraGroup * k] = hk;
                 q1 = fma(g, hk, q1);
                 cut += sk ? g : 0.0;
             }
             double q2 = 0.0;
             for (int k = 0; k < nu; k++) {
-                const double hk = hcol[32 * k];
+                const double hk = hcol[kSraGroup * k];
                 for (int e = sm.ptr[k]; e < sm.ptr[k + 1]; e++) {
                     const int l = sm.nb[e];
                     if (l > k) {
-                        const double dh = hk - hcol[32 * l];
+                        const double dh = hk - hcol[kSraGroup * l];
                         q2 = fma(sm.w[e], dh * dh, q2);
                     }
                 }
@@ -329,12 +332,15 @@ k_sra_pairs(const int* __restrict__ list, const int* __restrict__ count,
                 bmask = S;
             }
         }
-        // warp maximum, a fixed tree towards lane 0: larger energy, then smaller mask
-        for (int o = 16; o > 0; o >>= 1) {
-            const double on = __shfl_down_sync(0xffffffffu, bn, o);
-            const double oc = __shfl_down_sync(0xffffffffu, bc, o);
-            const uint32_t om = __shfl_down_sync(0xffffffffu, bmask, o);
-            if (lane + o < 32 && om != 0xFFFFFFFFu) {
+        // group maximum, a fixed tree towards lane 0 over the lanes that had candidates:
+        // larger energy, then smaller mask
+        const uint32_t used = min(total, (uint32_t)kSraGroup);
+        for (int o = kSraGroup / 2; o > 0; o >>= 1) {
+            if ((uint32_t)o >= used) continue;  // same for the whole group
+            const double on = __shfl_down_sync(gmask, bn, o, kSraGroup);
+            const double oc = __shfl_down_sync(gmask, bc, o, kSraGroup);
+            const uint32_t om = __shfl_down_sync(gmask, bmask, o, kSraGroup);
+            if (gl + o < kSraGroup && om != 0xFFFFFFFFu) {
                 bool take;
                 if (bmask == 0xFFFFFFFFu) take = true;
                 else {
@@ -348,18 +354,18 @@ k_sra_pairs(const int* __restrict__ list, const int* __restrict__ count,
                 }
             }
         }
-        bmask = __shfl_sync(0xffffffffu, bmask, 0);
+        bmask = __shfl_sync(gmask, bmask, 0, kSraGroup);
         // per evaluated split: g (2E adds), h (nu), q1 (nu FMAs), cut (nu), q2 (E times a
         // subtraction, a product and an FMA), the fraction and the comparison (5)
         ops += evals * (unsigned long long)(4 * nu + 3 * edges2 + 5);
         if (bmask == 0xFFFFFFFFu) continue;  // no admissible split: the pair stays as it is
         // the half holding local vertex 0 (the smallest vertex) keeps the smaller number I
         const bool zero_in_S = (bmask & 1u) != 0u;
-        if (lane < nu) {
-            const bool inS = ((bmask >> lane) & 1u) != 0u;
-            agg[sm.u[lane]] = (inS == zero_in_S) ? I : J;
+        if (gl < nu) {
+            const bool inS = ((bmask >> gl) & 1u) != 0u;
+            agg[sm.u[gl]] = (inS == zero_in_S) ? I : J;
         }
-        if (lane == 0) {
+        if (gl == 0) {
             const int cS = __popc(bmask);
             const int sizeI = zero_in_S ? cS : nu - cS;
             newsize[I] = sizeI;
@@ -416,7 +422,7 @@ int reshape_aggregation(Handle* h, int level, int n, const int* rowptr, const in
     const bool prof = (h->prof_class == UAAMG_KCLASS_SRA && level == 0);
     unsigned long long* flops = prof ? &h->ctrl->sra_flops : nullptr;
     if (prof) cudaMemsetAsync(flops, 0, sizeof(unsigned long long), h->work);
-    // persistent grid of warps over the pair list (at most nc / 2 pairs)
+    // persistent grid of half-warp groups over the pair list (at most nc / 2 pairs)
     static DevCache occ;
     int bps = occ.get(h->device);
     if (!bps) {
@@ -426,7 +432,7 @@ int reshape_aggregation(Handle* h, int level, int n, const int* rowptr, const in
             bps = 1;
         occ.set(h->device, bps);
     }
-    const long long need = ((long long)nc / 2 + kSraWarps - 1) / kSraWarps;
+    const long long need = ((long long)nc / 2 + 2 * kSraWarps - 1) / (2 * kSraWarps);
     const int pair_blocks = (int)std::max(1LL, std::min((long long)bps * h->num_sms, need));
     for (int r = 0; r < h->p.sra_rounds; r++) {
         const uint32_t salt = sra_round_salt(h->p.seed, level, r);
