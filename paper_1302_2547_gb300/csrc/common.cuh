@@ -19,7 +19,6 @@ constexpr int kThreads = 256;             // block size of every row / element k
 constexpr int kRowsPerBlock = 256;        // rows of one row-block SpMV block
 constexpr int kChunk = 2048;              // matrix entries staged in shared memory per step
 constexpr long long kBarrierTimeoutNs = 2000000000LL;  // bounded grid-barrier wait
-constexpr int kSraUnionMax = 16;          // largest union of a reshaped aggregate pair
 
 // error bits raised by device code into Ctrl::err
 constexpr int kErrTimeout = 1;
@@ -42,7 +41,6 @@ struct Ctrl {
     unsigned int pad0;
     int npasses;             // written by the aggregation kernel
     int pad[2];
-    unsigned long long sra_flops;  // FP64 operations of the profiled reshaping kernels
 };
 
 // FP64 scalars of one K-cycle level (Section 4.3).  Step 1 writes (rho1, alpha1), step 2

@@ -24,6 +24,7 @@
 // equal, and the smallest mask among them wins (symmetric splits have equal energies up to
 // rounding).
 #include "common.cuh"
+#include "kern_sra.cuh"
 #include "kernels.cuh"
 
 namespace uaamg {
@@ -420,7 +421,8 @@ int reshape_aggregation(Handle* h, int level, int n, const int* rowptr, const in
     int* mem2 = dalloc<int>(h, n, &st, true);
     if (st) return st;
     const bool prof = (h->prof_class == UAAMG_KCLASS_SRA && level == 0);
-    unsigned long long* flops = prof ? &h->ctrl->sra_flops : nullptr;
+    unsigned long long* flops = prof ? dalloc<unsigned long long>(h, 1, &st, true) : nullptr;
+    if (st) return st;
     if (prof) cudaMemsetAsync(flops, 0, sizeof(unsigned long long), h->work);
     // persistent grid of half-warp groups over the pair list (at most nc / 2 pairs)
     static DevCache occ;

@@ -42,11 +42,6 @@ int launch_compose(Handle* h, int n, int nc, const int* agg1, const int* aggptr1
                    const int* members1, const int* agg2, const int* aggptr2,
                    const int* members2, int* agg, int* aggptr, int* members, int* tmp,
                    int* scan_tmp);
-// subgraph reshaping (kern_sra.cu): rounds of Algorithm 3 on matched aggregate pairs
-uint32_t sra_round_salt(uint64_t seed, int level, int round);
-int reshape_aggregation(Handle* h, int level, int n, const int* rowptr, const int* col,
-                        const double* val, int nc, int* agg, int** aggptr, int** members,
-                        int* scan_tmp);
 int launch_level_finish(Handle* h, int n, long long nnz, const int* rowptr, const int* col,
                         const double* val64, double* minv64, float* minv32, float* val32);
 int launch_dense_coarsest(Handle* h, int n, const int* rowptr, const int* col,

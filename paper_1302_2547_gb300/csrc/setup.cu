@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "kern_sra.cuh"
 #include "kernels.cuh"
 
 namespace uaamg {
