@@ -1,7 +1,7 @@
 """Plain FP64 statement of subgraph reshaping (Section 3.2, Algorithm 3, Eq. 3.8).
 
-TEST INFRASTRUCTURE ONLY: imported by the tests and the CPU-baseline leg of the benchmark.
-The product package never imports this module, and it shares no code with the CUDA sources.
+TEST INFRASTRUCTURE ONLY: imported by the tests.  The product package never imports this
+module, and it shares no code with the CUDA sources.
 
 What it computes, step by step as the paper states it:
 
