@@ -229,7 +229,7 @@ def _golden_examples():
     rows = []
     with open(os.path.join(GOLDEN, "sra_examples.txt")) as f:
         for line in f:
-            if line.startswith("#") or not line.strip():
+            if not line.startswith("example"):
                 continue
             name, wh, wv, q2, e = line.split()
             rows.append((name, float(wh), float(wv), float(q2), float(e)))
@@ -361,3 +361,76 @@ def test_local_laplacian_of_a_subgraph(inputs):
     off = A - np.diag(np.diag(A))
     assert np.array_equal(A_hat - np.diag(np.diag(A_hat)), off)
     assert np.allclose(A_hat.sum(axis=1), 0.0, atol=0)  # Neumann: the Dirichlet part drops
+
+
+# ---------------------------------------------------------------------------------------
+# Section 5.1: the 16 x 16 grid aggregated with t = 5, then reshaped
+# ---------------------------------------------------------------------------------------
+
+def _grid16_golden():
+    with open(os.path.join(GOLDEN, "sra_examples.txt")) as f:
+        for line in f:
+            if line.startswith("grid16"):
+                return [float(x) for x in line.split()[1:]]
+    raise AssertionError("grid16 line missing")
+
+
+def _l2_energy(A, agg, nc):
+    """|Q|_A^2 of the l2 projection onto the piecewise constants (SPD A): the largest
+    generalised eigenvalue of Q^T A Q against A."""
+    n = A.shape[0]
+    P = np.zeros((n, nc))
+    P[np.arange(n), agg] = 1.0
+    Q = P @ np.linalg.solve(P.T @ P, P.T)
+    H = Q.T @ A @ Q
+    return float(sla.eigh(0.5 * (H + H.T), A, eigvals_only=True)[-1])
+
+
+def _two_level_rate(A, agg, nc, minv):
+    """|E|_A of the two-level method with one smoothing step before and after an exact
+    coarse solve: E = S (I - P A_c^{-1} P^T A) S, S = I - diag(minv) A."""
+    n = A.shape[0]
+    P = np.zeros((n, nc))
+    P[np.arange(n), agg] = 1.0
+    S = np.eye(n) - np.diag(minv) @ A
+    CG = np.eye(n) - P @ np.linalg.solve(P.T @ A @ P, P.T @ A)
+    E = S @ CG @ S
+    w, U = np.linalg.eigh(A)
+    half = U @ np.diag(np.sqrt(w)) @ U.T
+    ihalf = U @ np.diag(1.0 / np.sqrt(w)) @ U.T
+    return float(np.linalg.norm(half @ E @ ihalf, 2))
+
+
+def test_grid16_before_reshaping_matches_the_paper(oracle, inputs):
+    # the coarsening ratio, the l2-projection energy and the two-level rate (l1-Jacobi
+    # before and after, exact coarse solve) that Section 5.1 prints for this aggregation
+    side, t, ratio, q2_before, e_before, _, _ = _grid16_golden()
+    csr = inputs.grid2d(int(side), int(side), dirichlet=True)
+    agg, nc = _level0_aggregation(oracle, csr, t=int(t))
+    A = csr.dense()
+    assert round(csr.n / nc, 2) == ratio
+    assert round(_l2_energy(A, agg, nc), 2) == q2_before
+    minv = oracle.minv(csr.rowptr, csr.col, csr.val)
+    assert round(_two_level_rate(A, agg, nc, minv), 2) == e_before
+
+
+def test_grid16_reshaping_moves_as_the_paper_reports(oracle, inputs):
+    # The paper reshapes in an order it does not state, so only the direction is pinned:
+    # the energy of the l2 projection falls from 2.51 towards the printed 2.19, and the
+    # two-level rate does not improve (printed: 0.67 -> 0.69).  The number of aggregates
+    # is unchanged.
+    side, t, _, q2_before, e_before, q2_after, e_after = _grid16_golden()
+    csr = inputs.grid2d(int(side), int(side), dirichlet=True)
+    agg, nc = _level0_aggregation(oracle, csr, t=int(t))
+    A = csr.dense()
+    minv = oracle.minv(csr.rowptr, csr.col, csr.val)
+    a = agg
+    for r in range(8):
+        a = SRA.reshape_round(csr.rowptr, csr.col, csr.val, a, nc, 0x5EED, 0, r)
+        assert len(np.unique(a)) == nc
+        q2 = _l2_energy(A, a, nc)
+        e = _two_level_rate(A, a, nc, minv)
+        assert q2 < q2_before - 0.02, (r, q2)
+        if r >= 2:
+            assert abs(q2 - q2_after) <= 0.12, (r, q2)
+        assert e_before - 0.005 <= e <= e_after + 0.005, (r, e)
