@@ -39,3 +39,15 @@ def test_reference_line():
 def test_reference_other_ranks_are_silent():
     out = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert not [l for l in out.splitlines() if l.startswith("{")]
+
+
+def test_all_cores_oracle_baseline():
+    """The all-core oracle leg: spawned workers, one independent setup + solve each, timed
+    from the first start to the last finish."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+
+    d = bench.run_cpu_baseline_allcores(side=20, max_workers=2)
+    assert d["kind"] == "oracle" and d["unit"] == "solves/s"
+    assert 1 <= d["cores"] <= 2 and d["value"] > 0 and "20^3" in d["sample"]
