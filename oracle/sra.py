@@ -31,8 +31,9 @@ Readings where the paper is silent, ambiguous or garbled:
   vertex 0.  A candidate also needs a positive cut 1_S^T A_hat 1_S.  Symmetric splits have
   mathematically equal energies that FP64 rounds apart.  So energies within a relative
   TIE_REL count as equal: scanning the masks sum_{k in S} 2^k in ascending order, a
-  candidate replaces the best one only when its energy exceeds it by more than that.  The half holding local vertex 0 keeps
-  the smaller of the two aggregate numbers.  A pair without a candidate stays unchanged.
+  candidate replaces the best one only when its energy exceeds it by more than that.  The
+  half holding local vertex 0 keeps the smaller of the two aggregate numbers.  A pair
+  without a candidate stays unchanged.
 * The paper traverses the pairs of neighbouring aggregates without fixing an order.  Here a
   level is reshaped in rounds, and each round reshapes the pairs of a matching at once:
   - Aggregates I != J are neighbours when a stored fine entry a_st != 0 joins them.

@@ -72,7 +72,8 @@ k_sra_init(int nc, const int* __restrict__ aggptr, int* __restrict__ newsize,
 __global__ void __launch_bounds__(kThreads)
 k_sra_propose(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
               const double* __restrict__ val, const int* __restrict__ agg,
-              const int* __restrict__ aggptr, uint32_t salt, unsigned long long* __restrict__ prop) {
+              const int* __restrict__ aggptr, uint32_t salt,
+              unsigned long long* __restrict__ prop) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int I = agg[s];
