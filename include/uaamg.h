@@ -263,7 +263,8 @@ void uaamg_server_destroy(uaamg_server* s);
  * calling thread must not issue cudaMalloc/cudaFree while other work is in flight).
  *
  * Aggregates one graph level exactly as level 0 of uaamg_setup does (priorities, aggregation
- * passes with size limit max_agg_size and pass_mode, ascending coarse numbering) and writes
+ * passes with size limit max_agg_size and pass_mode, ascending coarse numbering; no
+ * subgraph reshaping, as with sra_rounds = 0) and writes
  * agg[i] = the coarse vertex of fine vertex i (device int32[n], caller-owned) and *nc (host)
  * = the number of aggregates.  A is validated like in uaamg_setup and must be on the device
  * (A->on_device = 1).  Nothing is allocated: all scratch lives in one static device array
