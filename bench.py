@@ -544,17 +544,23 @@ def run_cpu_baseline(sample_steps=1):
 
     O.build()
     A, b = workload()
-    t = []
+    t, ts, tv = [], [], []
     for _ in range(sample_steps):
         t0 = time.perf_counter()
         H = O.Hierarchy(A.rowptr, A.col, A.val, O.Params(**BENCH_PARAMS))
+        t1 = time.perf_counter()
         x, it, rr, st, _ = H.solve(b, TOL)
-        t.append(time.perf_counter() - t0)
+        t2 = time.perf_counter()
+        t.append(t2 - t0)
+        ts.append(t1 - t0)
+        tv.append(t2 - t1)
         assert st == 0
         del H
     return {"value": round(len(t) / sum(t), 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(t)} full setup+solve of the 128^3 system (serial C, FP64), "
-                      f"{sum(t):.1f} s"}, t, it
+                      f"{sum(t):.1f} s",
+            "setup_ms": round(1000 * float(np.median(ts)), 1),
+            "solve_ms": round(1000 * float(np.median(tv)), 1), "iterations": int(it)}, t, it
 
 
 def _mem_available() -> int:

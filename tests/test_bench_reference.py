@@ -31,6 +31,7 @@ def test_reference_line():
     assert d["config"]["workload"].startswith("laplace3d_128")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["setup_ms"] > 0 and cb["solve_ms"] > 0 and cb["iterations"] == d["iterations"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
