@@ -563,3 +563,40 @@ def test_damped_jacobi_closed_form_and_solve(oracle, inputs):
     b = inputs.rhs_uniform(A.n, 3)
     x, it, rr, st, _ = H.solve(b, 1e-8)
     assert st == 0 and np.linalg.norm(b - A.dense() @ x) <= 1e-8 * np.linalg.norm(b) * 1.0001
+
+
+@pytest.mark.parametrize("side", [14, 17])
+def test_kcycle_tau_threshold(oracle, inputs, side):
+    """The K-cycle threshold (Section 4.3, Notay's tau): the second flexible-CG step is
+    skipped exactly when |rho~| <= tau |rho|.  Just above the actual ratio K_1 is the one-step
+    e = (alpha1 / rho1) c1; just below it is the two-step combination, both computed densely
+    from the two-level B_1."""
+    A = inputs.grid2d(side, dirichlet=True)
+    base = oracle.Hierarchy(A.rowptr, A.col, A.val, oracle.Params(max_levels=3, coarse_size=8))
+    assert base.num_levels == 3
+    rp, cc, vv = base.csr(1)
+    n1 = base.n(1)
+    A1 = np.zeros((n1, n1))
+    A1[np.repeat(np.arange(n1), np.diff(rp)), cc] = vv
+    rp2, cc2, vv2 = base.csr(2)
+    n2 = base.n(2)
+    A2 = np.zeros((n2, n2))
+    A2[np.repeat(np.arange(n2), np.diff(rp2)), cc2] = vv2
+    B1 = BF.two_grid_B(A1, base.agg(1), n2, np.linalg.inv(A2))
+    rho = np.random.default_rng(side).standard_normal(n1)
+    c1 = B1 @ rho
+    v1 = A1 @ c1
+    rho1, alpha1 = c1 @ v1, c1 @ rho
+    rt = rho - (alpha1 / rho1) * v1
+    ratio = np.linalg.norm(rt) / np.linalg.norm(rho)
+    c2 = B1 @ rt
+    v2 = A1 @ c2
+    gamma, beta, alpha2 = c2 @ v1, c2 @ v2, c2 @ rt
+    rho2 = beta - gamma * gamma / rho1
+    two = (alpha1 / rho1 - gamma * alpha2 / (rho1 * rho2)) * c1 + (alpha2 / rho2) * c2
+    one = (alpha1 / rho1) * c1
+    for tau, expect in ((ratio * 1.01, one), (ratio * 0.99, two)):
+        H = oracle.Hierarchy(A.rowptr, A.col, A.val,
+                             oracle.Params(max_levels=3, coarse_size=8, kcycle_tau=tau))
+        assert np.allclose(H.apply_K(1, rho), expect, rtol=1e-9, atol=1e-12), tau
+    assert not np.allclose(one, two, rtol=1e-3)
