@@ -190,3 +190,49 @@ def test_full_size_round_one(oracle):
             first, other = (a, b) if best & 1 else (b, a)
             expect = np.array([first if best >> j & 1 else other for j in range(len(Uu))])
         assert np.array_equal(got[Uu], expect), (a, b)
+
+
+def oracle_levels_twice(oracle, A, p, nlev):
+    """As oracle_levels with aggregation applied twice per level (Section 3.3): stage 1
+    (priority salt index 2l) is reshaped, stage 2 (salt 2l+1) aggregates its coarse matrix,
+    and the level's aggregates are the unions."""
+    rp, cc, vv = A.rowptr, A.col, A.val
+    aggs, mats = [], [(rp, cc, vv)]
+    for l in range(nlev - 1):
+        P = oracle.priorities(rp, cc, p.seed, 2 * l)
+        root, _, _ = oracle.paa(rp, cc, P, p.max_agg_size, p.pass_mode)
+        a1, n1 = oracle.renumber(root)
+        a1 = SRA.reshape_level(rp, cc, vv, a1, n1, p.seed, l, p.sra_rounds)
+        r1, c1, v1 = oracle.coarse(rp, cc, vv, a1, n1)
+        agg, nxt = a1, (r1, c1, v1)
+        if n1 > p.coarse_size:
+            P2 = oracle.priorities(r1, c1, p.seed, 2 * l + 1)
+            root2, _, _ = oracle.paa(r1, c1, P2, p.max_agg_size, p.pass_mode)
+            a2, n2 = oracle.renumber(root2)
+            if n2 < n1:
+                agg, nxt = a2[a1], oracle.coarse(r1, c1, v1, a2, n2)
+        aggs.append(agg)
+        rp, cc, vv = nxt
+        mats.append(nxt)
+    return aggs, mats
+
+
+def test_reshaped_first_stage_of_double_aggregation(oracle):
+    """Reshaping with two aggregation stages per level (the benchmark's setting): stage 1 is
+    reshaped before stage 2 aggregates its coarse matrix; bit-exact with the oracle."""
+    A = I.grid3d(12, 11, 10, sigma=0.25, seed=5)
+    p = U.uaamg_default_params(sra_rounds=2, coarse_size=16, agg_repeat=2, max_agg_size=4)
+    h = U.uaamg_setup(A.rowptr, A.col, A.val, p)
+    try:
+        nlev = min(3, U.uaamg_num_levels(h))
+        assert nlev == 3
+        aggs, mats = oracle_levels_twice(oracle, A, p, nlev)
+        for l in range(nlev - 1):
+            got = U.uaamg_get_aggregates(h, l)
+            assert np.array_equal(got, aggs[l]), (l, int(np.sum(got != aggs[l])))
+            rp, cc, vv = U.uaamg_get_level_csr(h, l + 1)
+            orp, occ, ovv = mats[l + 1]
+            assert np.array_equal(rp, orp) and np.array_equal(cc, occ), l + 1
+            assert np.array_equal(bits(vv), bits(ovv)), l + 1
+    finally:
+        U.uaamg_free(h)
