@@ -600,3 +600,27 @@ def test_kcycle_tau_threshold(oracle, inputs, side):
                              oracle.Params(max_levels=3, coarse_size=8, kcycle_tau=tau))
         assert np.allclose(H.apply_K(1, rho), expect, rtol=1e-9, atol=1e-12), tau
     assert not np.allclose(one, two, rtol=1e-3)
+
+
+@pytest.mark.parametrize("pre,post", [(0, 1), (1, 0), (2, 2), (3, 1)])
+@pytest.mark.parametrize("omega", [0.0, 0.7])
+def test_two_level_error_propagation(oracle, inputs, pre, post, omega):
+    """Any number of smoothing sweeps (Algorithm 1 solve phase, Section 4.1): the two-level
+    B_0 satisfies I - B_0 A = S^post (I - P A_c^{-1} P^T A) S^pre with S = I - M^{-1} A
+    (l1-Jacobi, or damped Jacobi omega D^{-1}), from the closed forms of M^{-1}."""
+    A = inputs.grid2d(12, 9, dirichlet=True)
+    Ad = A.dense()
+    H = oracle.Hierarchy(A.rowptr, A.col, A.val,
+                         oracle.Params(max_levels=2, pre=pre, post=post, jacobi_omega=omega))
+    assert H.num_levels == 2
+    n, nc = A.n, H.n(1)
+    P = BF.prolongator(H.agg(0), nc)
+    Mi = np.diag(omega / np.diag(Ad)) if omega > 0 else np.diag(BF.l1_minv_dense(Ad))
+    S = np.eye(n) - Mi @ Ad
+    CG = np.eye(n) - P @ np.linalg.solve(P.T @ Ad @ P, P.T @ Ad)
+    E = np.linalg.matrix_power(S, post) @ CG @ np.linalg.matrix_power(S, pre)
+    B = (np.eye(n) - E) @ np.linalg.inv(Ad)
+    rng = np.random.default_rng(pre * 10 + post)
+    for _ in range(3):
+        r = rng.standard_normal(n)
+        assert np.allclose(H.apply_B(0, r), B @ r, rtol=1e-10, atol=1e-12)
