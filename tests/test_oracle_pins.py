@@ -624,3 +624,40 @@ def test_two_level_error_propagation(oracle, inputs, pre, post, omega):
     for _ in range(3):
         r = rng.standard_normal(n)
         assert np.allclose(H.apply_B(0, r), B @ r, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("side", [24, 31])
+def test_outer_iteration_is_pcg_for_a_linear_preconditioner(oracle, inputs, side):
+    """With two levels B_0 is linear and symmetric positive definite, and the outer flexible
+    CG with one stored direction (Sections 1 and 4.4) must coincide with textbook
+    preconditioned CG (Hestenes-Stiefel recurrences) run with the dense B_0."""
+    A = inputs.grid2d(side, dirichlet=True)
+    Ad = A.dense()
+    H = oracle.Hierarchy(A.rowptr, A.col, A.val, oracle.Params(max_levels=2))
+    assert H.num_levels == 2
+    nc = H.n(1)
+    P = BF.prolongator(H.agg(0), nc)
+    B = BF.two_grid_B(Ad, H.agg(0), nc, np.linalg.inv(P.T @ Ad @ P))
+    b = inputs.rhs_uniform(A.n, side)
+    x, it, rr, st, hist = H.solve(b, 1e-10)
+    assert st == 0
+    # textbook PCG from x0 = 0
+    r = b.copy()
+    z = B @ r
+    p = z.copy()
+    rz = r @ z
+    ref = [1.0]
+    for _ in range(it + 2):
+        q = Ad @ p
+        alpha = rz / (p @ q)
+        r = r - alpha * q
+        ref.append(np.linalg.norm(r) / np.linalg.norm(b))
+        z = B @ r
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    k = min(8, it)
+    assert np.allclose(hist[: k + 1], ref[: k + 1], rtol=1e-6)
+    # PCG first reaches the tolerance within one iteration of the oracle's count
+    first = next(j for j, v in enumerate(ref) if v <= 1e-10)
+    assert abs(first - it) <= 1
