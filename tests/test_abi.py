@@ -90,3 +90,69 @@ def test_product_never_imports_the_oracle():
                 for pat in (r"^\s*(from|import)\s+oracle\b", r"liboracle", r"oracle/",
                             r"uaamg_oracle"):
                     assert not re.search(pat, text, flags=re.M), (f, pat)
+
+
+def test_binding_constants_match_the_header():
+    """Every UAAMG_* constant that the Python binding restates has the header's value."""
+    from paper_1302_2547_gb300 import _lib as U
+
+    text = open(os.path.join(ROOT, "include", "uaamg.h")).read()
+    defs = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"#define\s+(UAAMG_\w+)\s+(-?\d+)", text)}
+    restated = [n for n in dir(U) if n.startswith("UAAMG_")]
+    assert len(restated) >= 10
+    for name in restated:
+        assert name in defs, name
+        assert getattr(U, name) == defs[name], name
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """The ctypes mirrors of uaamg_csr, uaamg_params and uaamg_stats have the C layout:
+    a probe compiled against include/uaamg.h prints every field's offset and the size."""
+    from paper_1302_2547_gb300 import _lib as U
+
+    structs = {"uaamg_csr": U.uaamg_csr, "uaamg_params": U.uaamg_params,
+               "uaamg_stats": U.uaamg_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "uaamg.h"',
+             'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {}
+    for line in out.splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_binding_structs_have_every_header_field():
+    """Field names and order of the ctypes mirrors equal the header's declarations (a field
+    missing at the end could hide in the padding of the size check)."""
+    from paper_1302_2547_gb300 import _lib as U
+
+    text = open(os.path.join(ROOT, "include", "uaamg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    for cname, py in (("uaamg_csr", U.uaamg_csr), ("uaamg_params", U.uaamg_params),
+                      ("uaamg_stats", U.uaamg_stats)):
+        body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (cname, cname), text, re.S).group(1)
+        names = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            # "const int32_t* rowptr" / "int32_t pre, post": the declarators follow the type
+            parts = [p.strip() for p in decl.split(",")]
+            names.append(re.findall(r"(\w+)\s*$", parts[0])[0])
+            names += [re.findall(r"(\w+)\s*$", p)[0] for p in parts[1:]]
+        assert names == [f for f, _ in py._fields_], cname
