@@ -661,3 +661,21 @@ def test_outer_iteration_is_pcg_for_a_linear_preconditioner(oracle, inputs, side
     # PCG first reaches the tolerance within one iteration of the oracle's count
     first = next(j for j, v in enumerate(ref) if v <= 1e-10)
     assert abs(first - it) <= 1
+
+
+def test_oracle_params_mirror_the_c_struct(oracle):
+    """The ctypes mirror of the oracle's parameter struct has the C struct's fields in order."""
+    import re
+
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "oracle", "uaamg_oracle.c")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct or_params \{(.*?)\} or_params;", src, re.S).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            parts = [p.strip() for p in decl.split(",")]
+            names.append(re.findall(r"(\w+)\s*$", parts[0])[0])
+            names += [re.findall(r"(\w+)\s*$", p)[0] for p in parts[1:]]
+    assert names == [f for f, _ in oracle._Params._fields_]
