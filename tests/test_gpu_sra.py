@@ -131,8 +131,8 @@ def test_profile_class_counts_the_pair_kernel():
         U.uaamg_free(h)
 
 
-def test_full_size_round_one(oracle):
-    """128^3 with lognormal weights, device-resident input, one round on level 0."""
+def test_full_size_first_reshaping_round(oracle):
+    """128^3 with lognormal weights, device-resident input, one reshaping round on level 0."""
     import torch
 
     from bench import BENCH_PARAMS
