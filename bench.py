@@ -192,6 +192,7 @@ def run_gpu(args, rank, world):
             if st != 0:
                 raise RuntimeError(f"solve status {st} after {it} iterations, relres {rr}")
             s = U.uaamg_get_stats(h)
+            s["levels"] = U.uaamg_num_levels(h)
             prof = U.uaamg_get_profile(h) if profile_class else None
             return it, rr, s, prof
         finally:
@@ -349,7 +350,8 @@ def run_gpu(args, rank, world):
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                        "p99": round(float(np.percentile(lat, 99)), 3)},
         "iterations": int(np.median(its)), "relres_host_fp64": relres_host,
-        "levels": None, "opc": round(stats["opc"], 3),
+        "levels": stats["levels"], "opc": round(stats["opc"], 3),
+        "grid_complexity": round(stats["grid_complexity"], 3),
         "plain_fp64": None if not p_rec else {
             "value": round(len(p_lat) / (p_total / 1000.0), 3), "unit": "solves/s",
             "setup_ms": round(float(np.median([r[2]['setup_ms'] for r in p_rec])), 3),
