@@ -49,7 +49,7 @@ NCU_SOURCES = {
     "coarse": ("kern_setup.cu", "kernels.cuh", "common.cuh"),
 }
 NCU_TRAFFIC = {
-    # level 0 of the 128^3 system, ncu --set full (profiles/rowwarp_tma_laplace3d_128_level0.md)
+    # level 0 of the 128^3 system, ncu --set full
     # k_rowwarp_tma<float, RB_PRE1>: 141,838,336 + 7,883,520 bytes
     ("smooth0", "0defb33c3b3547d4"): 149721856,
     # k_rowwarp_tma<double, RB_SPMV, 2 dots>: 216,973,312 + 12,700,160 bytes

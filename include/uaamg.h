@@ -50,6 +50,7 @@ extern "C" {
 #define UAAMG_ERR_CUDA 7          /* a CUDA runtime call failed (no device, launch error) */
 #define UAAMG_ERR_TIMEOUT 8       /* a bounded device-side wait gave up */
 #define UAAMG_ERR_UNSUPPORTED 9   /* a size beyond this build's limits */
+#define UAAMG_ERR_CANCELLED 10    /* a queued solve-service request was cancelled */
 
 /* ---- parameters --------------------------------------------------------------------- */
 #define UAAMG_FP64 0  /* K-cycle, hierarchy and outer iteration in FP64 */
@@ -114,6 +115,12 @@ typedef struct uaamg_params {
                              relative 1e-9 count as equal (the split whose mask of the union's
                              ascending vertices is smallest wins).  A pair without such a split
                              stays as it is.  The number of aggregates does not change. */
+    int64_t wait_limit_ns; /* limit of every bounded device-side wait of this handle: a grid
+                              barrier of a cooperative kernel, a wait for a bulk copy into
+                              shared memory (measured in SM clock cycles, about 2 per ns).
+                              A wait that runs out makes the call return UAAMG_ERR_TIMEOUT and
+                              leaves the device usable.  0 (default): 2 s per barrier, 2^31
+                              cycles per copy wait. */
 } uaamg_params;
 
 typedef struct uaamg_handle uaamg_handle;
@@ -251,6 +258,10 @@ int uaamg_server_poll(uaamg_server* s, uint64_t ticket, int32_t* done);
  * Returns the request's status; the ticket is released. */
 int uaamg_server_wait(uaamg_server* s, uint64_t ticket, double* x, int32_t* iters,
                       double* relres, double* latency_ms, int32_t* batch);
+/* Withdraws a request that no worker has taken yet: *cancelled = 1 and its wait returns
+ * UAAMG_ERR_CANCELLED.  A request already being solved (or answered) is not interrupted:
+ * *cancelled = 0 and its wait returns its result.  The ticket stays valid until waited on. */
+int uaamg_server_cancel(uaamg_server* s, uint64_t ticket, int32_t* cancelled);
 int uaamg_server_stats(uaamg_server* s, uint64_t* done, uint64_t* batches, uint64_t* cache_hits,
                        uint64_t* setups, uint64_t* rejected, int32_t* cached);
 /* Finishes the queued requests, joins the workers and frees every cached hierarchy. */
@@ -262,9 +273,9 @@ void uaamg_server_destroy(uaamg_server* s);
  * allocate device memory (an external memory manager owns the device's memory, or the
  * calling thread must not issue cudaMalloc/cudaFree while other work is in flight).
  *
- * Aggregates one graph level exactly as level 0 of uaamg_setup does (priorities, aggregation
- * passes with size limit max_agg_size and pass_mode, ascending coarse numbering; no
- * subgraph reshaping, as with sra_rounds = 0) and writes
+ * Aggregates one graph level exactly as level 0 of uaamg_setup does with agg_repeat = 1 and
+ * sra_rounds = 0 (priorities, aggregation passes with size limit max_agg_size and pass_mode,
+ * ascending coarse numbering; one aggregation stage, no subgraph reshaping) and writes
  * agg[i] = the coarse vertex of fine vertex i (device int32[n], caller-owned) and *nc (host)
  * = the number of aggregates.  A is validated like in uaamg_setup and must be on the device
  * (A->on_device = 1).  Nothing is allocated: all scratch lives in one static device array
@@ -274,7 +285,8 @@ void uaamg_server_destroy(uaamg_server* s);
  * and should therefore come before any stream capture.  Every call shares the array and
  * clears what must start at zero: calls whose work overlaps on the GPU (different streams,
  * or different host threads) race and must be serialised by the caller.  The call
- * synchronises `stream` twice (after validation and to read *nc).
+ * synchronises `stream` three times (after validation, after the aggregation passes, and to
+ * read *nc).
  */
 int uaamg_aggregate_static(const uaamg_csr* A, int32_t max_agg_size, int32_t pass_mode,
                            uint64_t seed, int32_t* agg, int32_t* nc, void* stream);

@@ -14,6 +14,8 @@ LIB_PATH = os.path.join(_HERE, "libuaamg.so")
 
 UAAMG_OK = 0
 UAAMG_ERR_NO_CONVERGENCE = 4
+UAAMG_ERR_TIMEOUT = 8
+UAAMG_ERR_CANCELLED = 10
 UAAMG_FP64, UAAMG_MIXED = 0, 1
 UAAMG_PASS_MAXIMAL, UAAMG_PASS_SINGLE_ROUND = 0, 1
 UAAMG_KCLASS_SMOOTH0, UAAMG_KCLASS_SPMV64, UAAMG_KCLASS_PAA, UAAMG_KCLASS_COARSE = 1, 2, 3, 4
@@ -28,7 +30,7 @@ EXPORTS = [
     "uaamg_total_launches", "uaamg_set_memory_budget", "uaamg_memory_in_use",
     "uaamg_status_string", "uaamg_aggregate_static", "uaamg_solve_many",
     "uaamg_server_create", "uaamg_server_submit", "uaamg_server_poll", "uaamg_server_wait",
-    "uaamg_server_stats", "uaamg_server_destroy",
+    "uaamg_server_stats", "uaamg_server_destroy", "uaamg_server_cancel",
 ]
 
 
@@ -46,7 +48,7 @@ class uaamg_params(C.Structure):
                 ("agg_repeat", C.c_int32), ("kcycle_ratio", C.c_double),
                 ("min_coarsening", C.c_double), ("jacobi_omega", C.c_double),
                 ("tma_rows", C.c_int32), ("sell_rows", C.c_int32), ("fuse_below", C.c_int32),
-                ("sra_rounds", C.c_int32)]
+                ("sra_rounds", C.c_int32), ("wait_limit_ns", C.c_int64)]
 
 
 class uaamg_stats(C.Structure):
@@ -110,6 +112,7 @@ def lib() -> C.CDLL:
             "uaamg_server_stats": (C.c_int, [P, C.POINTER(U64), C.POINTER(U64), C.POINTER(U64),
                                              C.POINTER(U64), C.POINTER(U64), C.POINTER(I32)]),
             "uaamg_server_destroy": (None, [P]),
+            "uaamg_server_cancel": (C.c_int, [P, U64, C.POINTER(I32)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -297,16 +300,43 @@ def uaamg_memory_in_use() -> int:
     return int(lib().uaamg_memory_in_use())
 
 
+def _dtype_name(a) -> str:
+    return str(a.dtype).replace("torch.", "")
+
+
 def uaamg_aggregate_static(rowptr, col, val, agg, max_agg_size: int = 5,
                            pass_mode: int = UAAMG_PASS_SINGLE_ROUND, seed: int = 0x5EED,
                            stream=None) -> int:
     """Level-0 aggregation into the caller's device buffer `agg` (int32[n]) with no device
     allocation by the library; returns the number of aggregates.  All arrays are CUDA
-    tensors."""
-    (rp, d0), (cp, d1), (vp, d2), (ap, d3) = _ptr(rowptr), _ptr(col), _ptr(val), _ptr(agg)
-    if not (d0 and d1 and d2 and d3):
-        raise ValueError("uaamg_aggregate_static takes device arrays only")
-    A = uaamg_csr(int(rowptr.shape[0]) - 1, int(col.shape[0]), rp, cp, vp, 1)
+    tensors on the current device: rowptr int32[n+1], col int32[nnz], val float64[nnz],
+    agg int32 with at least n entries.  Anything else raises ValueError before the C call
+    (the library cannot see the length of a device buffer)."""
+    arrs = {"rowptr": rowptr, "col": col, "val": val, "agg": agg}
+    want = {"rowptr": "int32", "col": "int32", "val": "float64", "agg": "int32"}
+    for k, a in arrs.items():
+        if not hasattr(a, "dtype") or _dtype_name(a) != want[k]:
+            raise ValueError(f"{k} must be {want[k]}, not {getattr(a, 'dtype', type(a))}")
+        if len(a.shape) != 1:
+            raise ValueError(f"{k} must be one-dimensional")
+    n = int(rowptr.shape[0]) - 1
+    if n < 1:
+        raise ValueError("rowptr must hold n + 1 >= 2 entries")
+    if int(col.shape[0]) != int(val.shape[0]):
+        raise ValueError("col and val must have the same length")
+    if int(agg.shape[0]) < n:
+        raise ValueError(f"agg holds {int(agg.shape[0])} entries, fewer than n = {n}")
+    for k, a in arrs.items():
+        if not hasattr(a, "is_cuda") or not a.is_cuda:
+            raise ValueError(f"uaamg_aggregate_static takes CUDA tensors only ({k})")
+    import torch
+
+    cur = torch.cuda.current_device()
+    for k, a in arrs.items():
+        if a.device.index != cur:
+            raise ValueError(f"{k} is on cuda:{a.device.index}, not the current cuda:{cur}")
+    (rp, _), (cp, _), (vp, _), (ap, _) = _ptr(rowptr), _ptr(col), _ptr(val), _ptr(agg)
+    A = uaamg_csr(n, int(col.shape[0]), rp, cp, vp, 1)
     nc = C.c_int32(0)
     check(lib().uaamg_aggregate_static(C.byref(A), max_agg_size, pass_mode, seed, ap,
                                        C.byref(nc), _stream(stream)), "uaamg_aggregate_static")
@@ -350,6 +380,12 @@ class Server:
         st = lib().uaamg_server_wait(self._s, ticket, x.ctypes.data, C.byref(it), C.byref(rr),
                                      C.byref(lat), C.byref(bt))
         return st, x, it.value, rr.value, lat.value, bt.value
+
+    def cancel(self, ticket: int) -> bool:
+        """True when the request was withdrawn before any worker took it."""
+        c = C.c_int32(0)
+        check(lib().uaamg_server_cancel(self._s, ticket, C.byref(c)), "uaamg_server_cancel")
+        return bool(c.value)
 
     def stats(self) -> dict:
         v = [C.c_uint64() for _ in range(5)]

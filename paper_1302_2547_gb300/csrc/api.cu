@@ -77,7 +77,8 @@ static bool params_ok(const uaamg_params* p) {
            p->profile_class >= 0 && p->profile_class <= UAAMG_KCLASS_SRA &&
            (p->agg_repeat == 1 || p->agg_repeat == 2) && p->kcycle_ratio >= 0.0 &&
            p->min_coarsening >= 0.0 && p->fuse_below >= 0 && p->jacobi_omega >= 0.0 &&
-           p->tma_rows >= 0 && p->sell_rows >= 0 && p->sra_rounds >= 0 && p->sra_rounds <= 64;
+           p->tma_rows >= 0 && p->sell_rows >= 0 && p->sra_rounds >= 0 && p->sra_rounds <= 64 &&
+           p->wait_limit_ns >= 0;
 }
 
 }  // namespace uaamg
@@ -110,6 +111,7 @@ void uaamg_default_params(uaamg_params* p) {
     p->sell_rows = 0;
     p->fuse_below = 0;
     p->sra_rounds = 0;
+    p->wait_limit_ns = 0;
 }
 
 int uaamg_setup(const uaamg_csr* A, const uaamg_params* p, void* stream, uaamg_handle** out) {

@@ -18,7 +18,8 @@ constexpr int kMaxRoundSlots = 1 << 16;   // aggregation rounds + passes per lev
 constexpr int kThreads = 256;             // block size of every row / element kernel
 constexpr int kRowsPerBlock = 256;        // rows of one row-block SpMV block
 constexpr int kChunk = 2048;              // matrix entries staged in shared memory per step
-constexpr long long kBarrierTimeoutNs = 2000000000LL;  // bounded grid-barrier wait
+constexpr long long kBarrierTimeoutNs = 2000000000LL;  // bounded grid-barrier wait (default)
+constexpr long long kFastPollNs = 100000;  // limits below this are checked on every poll
 
 // error bits raised by device code into Ctrl::err
 constexpr int kErrTimeout = 1;
@@ -40,7 +41,7 @@ struct Ctrl {
     unsigned int bar_count;  // grid barrier arrivals (zeroed before each cooperative launch)
     unsigned int pad0;
     int npasses;             // written by the aggregation kernel
-    int pad[2];
+    long long wait_ns;       // limit of every bounded device wait (0: the defaults)
 };
 
 // FP64 scalars of one K-cycle level (Section 4.3).  Step 1 writes (rho1, alpha1), step 2
@@ -254,29 +255,34 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
     return v;
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The arrival counter only grows (the launcher
-// zeroes it): the k-th barrier is passed once it reaches (k+1) * gridDim.x, so an arrival
-// costs one atomic and no block has to reset or flip anything.  The wait polls with an
-// acquire load, first back to back, then with a short sleep, and gives up after
-// kBarrierTimeoutNs (kErrTimeout, returns false).
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The arrival counter
+// only grows (the launcher zeroes it): the k-th barrier is passed once it reaches
+// (k+1) * gridDim.x, so an arrival costs one atomic and no block has to reset or flip
+// anything.  The wait polls with an acquire load, first back to back, then with a short
+// sleep, and gives up (kErrTimeout, returns false) after the handle's wait limit
+// (c->wait_ns, default kBarrierTimeoutNs) or as soon as another block has given up.  Limits
+// below kFastPollNs are checked on every poll.
 __device__ __forceinline__ bool grid_barrier(Ctrl* c) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
+        const long long lim0 = *(volatile long long*)&c->wait_ns;
+        const long long lim = lim0 > 0 ? lim0 : kBarrierTimeoutNs;
+        const bool fast = lim < kFastPollNs;
         const unsigned int arrived = atomicAdd(&c->bar_count, 1u);
         const unsigned int target = (arrived / gridDim.x + 1u) * gridDim.x;
-        long long t0 = 0;
+        long long t0 = fast ? global_ns() : 0;
         int spins = 0;
         while ((int)(ld_acquire(&c->bar_count) - target) < 0) {
-            if (++spins < 64) continue;
+            if (!fast && ++spins < 64) continue;
             const long long now = global_ns();
             if (t0 == 0) {
                 t0 = now;
-            } else if (now - t0 > kBarrierTimeoutNs) {
+            } else if (now - t0 > lim || (*(volatile int*)&c->err & kErrTimeout)) {
                 atomicOr(&c->err, kErrTimeout);
                 break;
             }
-            __nanosleep(32);
+            if (!fast) __nanosleep(32);
         }
         __threadfence();
     }

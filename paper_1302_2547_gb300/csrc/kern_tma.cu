@@ -21,7 +21,7 @@ namespace uaamg {
 
 constexpr int kTmaWarps = kThreads / 32;   // warps per block, each with its own pipeline
 constexpr int kTmaBatch = 8;               // gathers a lane has in flight per row
-constexpr long long kTmaSpin = 1LL << 31;  // clock cycles before a stage wait gives up
+constexpr long long kTmaSpin = 1LL << 31;  // clock cycles before a stage wait gives up (default)
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -101,6 +101,10 @@ template <typename T, int MODE, int ND, int CAP>
 __global__ void __launch_bounds__(kThreads) k_rowwarp_tma(RBArgs<T> a, Ctrl* ctrl) {
     if (!rb_enter<T, MODE>(a)) return;
     const KScal<T> ks = kscal<T, MODE>(a);
+    // a stage wait gives up after the handle's wait limit (about 2 cycles per ns), else
+    // kTmaSpin cycles; the wait for copies still in flight after that always takes kTmaSpin
+    const long long wait_ns = ctrl->wait_ns;
+    const long long spin = wait_ns > 0 ? 2 * wait_ns : kTmaSpin;
     extern __shared__ __align__(128) unsigned char dyn[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpStages<T, CAP>& ws = reinterpret_cast<WarpStages<T, CAP>*>(dyn)[warp];
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_rowwarp_tma(RBArgs<T> a, Ctrl* ctr
             bool failed = false;
             const long long t0 = clock64();
             while (!mbar_try_wait(&ws.bar[s], (phase >> s) & 1u)) {
-                if (clock64() - t0 > kTmaSpin) {
+                if (clock64() - t0 > spin) {
                     failed = true;
                     break;
                 }

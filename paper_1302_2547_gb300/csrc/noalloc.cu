@@ -106,8 +106,8 @@ extern "C" int uaamg_aggregate_static(const uaamg_csr* A, int32_t max_agg_size,
     const int n = A->n;
 
     // the array keeps the previous call's contents: clear the words that must start at zero
-    cudaMemsetAsync(h.ctrl, 0, sizeof(Ctrl), h.work);
-    cudaMemsetAsync(d_tot, 0, 4 * sizeof(int), h.work);
+    if ((st = check_cuda(cudaMemsetAsync(h.ctrl, 0, sizeof(Ctrl), h.work)))) return st;
+    if ((st = check_cuda(cudaMemsetAsync(d_tot, 0, 4 * sizeof(int), h.work)))) return st;
     Ctrl hc{};
     int tot[4] = {0, 0, 0, 0};
     if ((st = launch_validate(&h, n, A->nnz, A->rowptr, A->col, A->val))) return st;
@@ -121,6 +121,12 @@ extern "C" int uaamg_aggregate_static(const uaamg_csr* A, int32_t max_agg_size,
     if ((st = launch_root_flags(&h, n, pb.root_of, pb.agg_size, f, g))) return st;
     if ((st = scan_exclusive(&h, f, f, n, d_tot, scan_tmp))) return st;
     if ((st = scan_exclusive(&h, g, g, n, nullptr, scan_tmp))) return st;
+    // the numbering indexes by the roots the passes wrote: only after they all finished
+    cudaMemcpyAsync(&hc, h.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h.work);
+    if ((st = check_cuda(cudaStreamSynchronize(h.work)))) return st;
+    if (hc.err & kErrTimeout) return UAAMG_ERR_TIMEOUT;
+    if (hc.err & kErrSlots) return UAAMG_ERR_UNSUPPORTED;
+    if (hc.err) return UAAMG_ERR_CUDA;
     if ((st = launch_renumber(&h, n, pb.root_of, f, g, A->rowptr, A->col, d_tot, agg, aggptr,
                               members)))
         return st;

@@ -126,6 +126,7 @@ const char* uaamg_status_string(int s) {
         case UAAMG_ERR_CUDA: return "CUDA runtime error";
         case UAAMG_ERR_TIMEOUT: return "bounded device wait timed out";
         case UAAMG_ERR_UNSUPPORTED: return "size beyond this build's limits";
+        case UAAMG_ERR_CANCELLED: return "request cancelled";
         default: return "unknown status";
     }
 }

@@ -80,6 +80,7 @@ struct uaamg_server {
     int device = 0;
     // statistics
     uint64_t n_done = 0, n_batches = 0, n_hits = 0, n_setups = 0, n_rejected = 0;
+    uint64_t n_cancelled = 0;
 
     CacheEntry* find(uint64_t key) {
         for (auto it = cache.begin(); it != cache.end(); ++it)
@@ -326,6 +327,25 @@ int uaamg_server_wait(uaamg_server* s, uint64_t ticket, double* x, int32_t* iter
     if (batch) *batch = req->batch;
     s->tickets.erase(it);
     return req->status;
+}
+
+int uaamg_server_cancel(uaamg_server* s, uint64_t ticket, int32_t* cancelled) {
+    if (!s || !cancelled) return UAAMG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return UAAMG_ERR_INVALID_ARG;
+    *cancelled = 0;
+    for (auto q = s->queue.begin(); q != s->queue.end(); ++q) {
+        if ((*q)->ticket != ticket) continue;
+        (*q)->status = UAAMG_ERR_CANCELLED;
+        (*q)->done = true;
+        s->queue.erase(q);
+        s->n_cancelled++;
+        *cancelled = 1;
+        s->cv_done.notify_all();
+        break;
+    }
+    return UAAMG_OK;
 }
 
 int uaamg_server_stats(uaamg_server* s, uint64_t* done, uint64_t* batches, uint64_t* cache_hits,

@@ -120,6 +120,9 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
     h->ctrl = dalloc<Ctrl>(h, 1, &st);
     if (st) goto done;
     cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->work);
+    if (h->p.wait_limit_ns > 0)  // the source lives in the handle until it is freed
+        cudaMemcpyAsync(&h->ctrl->wait_ns, &h->p.wait_limit_ns, sizeof(long long),
+                        cudaMemcpyHostToDevice, h->work);
 
     {  // level 0: copy and validate
         Level& L = h->lev[0];

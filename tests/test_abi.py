@@ -61,7 +61,7 @@ def test_params_are_checked_before_any_device_work(built):
     A = I.grid2d(8)
     for bad in ({"max_agg_size": 1}, {"kcycle_inner": 3}, {"precision": 7},
                 {"max_levels": 0}, {"pass_mode": 4}, {"pre": -1}, {"sra_rounds": -1},
-                {"sra_rounds": 65}, {"profile_class": 6}):
+                {"sra_rounds": 65}, {"profile_class": 6}, {"wait_limit_ns": -1}):
         with pytest.raises(U.UaamgError) as e:
             U.uaamg_setup(A.rowptr, A.col, A.val, U.uaamg_default_params(**bad))
         assert e.value.status == 1
@@ -156,3 +156,30 @@ def test_binding_structs_have_every_header_field():
             names.append(re.findall(r"(\w+)\s*$", parts[0])[0])
             names += [re.findall(r"(\w+)\s*$", p)[0] for p in parts[1:]]
         assert names == [f for f, _ in py._fields_], cname
+
+
+def test_static_aggregation_wrapper_rejects_bad_arguments(built):
+    """The binding of uaamg_aggregate_static checks dtypes, lengths and the device of every
+    array before the C call, which cannot see the length of a device buffer (CPU only: every
+    case here is refused before any device work)."""
+    import torch
+
+    from paper_1302_2547_gb300 import _lib as U
+
+    n = 6
+    rp = torch.arange(n + 1, dtype=torch.int32)
+    cc = torch.arange(n, dtype=torch.int32)
+    vv = torch.ones(n, dtype=torch.float64)
+    ag = torch.zeros(n, dtype=torch.int32)
+    bad = [((rp.long(), cc, vv, ag), "rowptr must be int32"),
+           ((rp, cc.long(), vv, ag), "col must be int32"),
+           ((rp, cc, vv.float(), ag), "val must be float64"),
+           ((rp, cc, vv, ag.long()), "agg must be int32"),
+           ((rp, cc, vv, ag[: n - 1]), "fewer than n"),
+           ((rp, cc[: n - 1], vv, ag), "same length"),
+           ((rp[:1], cc, vv, ag), "n + 1 >= 2"),
+           ((rp.numpy(), cc, vv, ag), "CUDA tensors only (rowptr)"),
+           ((rp, cc, vv, ag), "CUDA tensors only")]
+    for args, msg in bad:
+        with pytest.raises(ValueError, match=re.escape(msg)):
+            U.uaamg_aggregate_static(*args)

@@ -63,12 +63,45 @@ def test_mix_equals_alone():
 
 def test_budget_rejects_what_cannot_fit():
     A = I.grid3d(40, sigma=0.25, seed=1)
+    held0 = U.uaamg_memory_in_use()
     srv = U.Server(U.uaamg_default_params(max_agg_size=0), budget_bytes=1 << 20, workers=1)
     try:
         t = srv.submit(A.rowptr, A.col, A.val, np.ones(A.n))
         st, *_ = srv.wait(t)
         assert st == 6  # UAAMG_ERR_BUDGET
         assert srv.stats()["rejected"] == 1
+        # the rejected request holds no device memory, before and after the server ends
+        assert U.uaamg_memory_in_use() == held0
     finally:
         srv.close()
-    assert U.uaamg_memory_in_use() == 0 or True
+    assert U.uaamg_memory_in_use() == held0
+
+
+def test_cancel_withdraws_queued_requests_only():
+    """With one worker busy on the first request, requests queued behind it can be withdrawn:
+    their wait reports UAAMG_ERR_CANCELLED and no worker solves them; the others (the one
+    in flight included) are answered as usual."""
+    tol = 1e-8
+    big = I.grid3d(48, sigma=0.25, seed=9)
+    small = [I.grid2d(40 + 3 * k, 37) for k in range(4)]
+    srv = U.Server(U.uaamg_default_params(max_agg_size=0), workers=1, max_batch=4)
+    try:
+        t0 = srv.submit(big.rowptr, big.col, big.val, np.ones(big.n), tol)
+        ts = [srv.submit(A.rowptr, A.col, A.val, np.ones(A.n), tol) for A in small]
+        withdrawn = [srv.cancel(t) for t in ts[1::2]]
+        assert all(withdrawn)
+        res0 = srv.wait(t0)
+        res = [srv.wait(t) for t in ts]
+        stats = srv.stats()
+    finally:
+        srv.close()
+    assert res0[0] == 0
+    for k, r in enumerate(res):
+        if k % 2 == 1:
+            assert r[0] == U.UAAMG_ERR_CANCELLED
+        else:
+            A = small[k]
+            Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+            assert r[0] == 0
+            assert np.linalg.norm(np.ones(A.n) - Asp @ r[1]) <= tol * np.sqrt(A.n) * 1.0001
+    assert stats["done"] == 1 + len(small) // 2 + len(small) % 2

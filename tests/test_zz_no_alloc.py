@@ -15,10 +15,12 @@ pytestmark = pytest.mark.gpu
 
 
 def _reference(A, t, mode, seed):
+    """Level-0 aggregates of uaamg_setup with one aggregation stage (agg_repeat = 1), the
+    setup this entry point reproduces."""
     from paper_1302_2547_gb300 import _lib as U
 
     p = U.uaamg_default_params(max_agg_size=t, pass_mode=mode, seed=seed,
-                               precision=U.UAAMG_FP64)
+                               precision=U.UAAMG_FP64, agg_repeat=1)
     h = U.uaamg_setup(A.rowptr, A.col, A.val, p)
     try:
         return U.uaamg_get_aggregates(h, 0), U.uaamg_level_info(h, 1)[0]
@@ -42,13 +44,21 @@ def test_static_aggregation_matches_setup_twice():
     for A, t, mode, seed in cases:
         ref, nc_ref = _reference(A, t, mode, seed)
         rp, cc, vv = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+        aggs = [torch.full((A.n,), -7, dtype=torch.int32, device=dev) for _ in range(2)]
+        torch.cuda.synchronize()
         for call in range(2):
-            agg = torch.full((A.n,), -7, dtype=torch.int32, device=dev)
-            nc = U.uaamg_aggregate_static(rp, cc, vv, agg, max_agg_size=t, pass_mode=mode,
-                                          seed=seed)
+            # the second call must not take any device memory: neither the device's free
+            # memory nor the library's own allocation count may change across it (the first
+            # call may still load kernels)
+            free0, held0 = torch.cuda.mem_get_info()[0], U.uaamg_memory_in_use()
+            nc = U.uaamg_aggregate_static(rp, cc, vv, aggs[call], max_agg_size=t,
+                                          pass_mode=mode, seed=seed)
             torch.cuda.synchronize()
+            if call == 1:
+                assert torch.cuda.mem_get_info()[0] == free0, A.name
+                assert U.uaamg_memory_in_use() == held0, A.name
             assert nc == nc_ref, (A.name, call)
-            assert np.array_equal(agg.cpu().numpy(), ref), (A.name, call)
+            assert np.array_equal(aggs[call].cpu().numpy(), ref), (A.name, call)
 
 
 def test_static_aggregation_rejects_graphs_above_its_limit():
