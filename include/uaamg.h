@@ -168,6 +168,44 @@ int uaamg_solve(uaamg_handle* h, const double* b, double* x, double tol, int32_t
 int uaamg_solve_many(uaamg_handle* h, int32_t nrhs, const double* B, double* X, double tol,
                      int32_t* iters, double* relres);
 
+/*
+ * Solves nsys independent systems together, each with its own hierarchy (a handle from
+ * uaamg_setup, all on one device and in one precision, pre = post = 1) and its own nrhs[s]
+ * right-hand sides (1 <= nrhs[s] <= 32).  Every column of every system runs the same
+ * algorithm as uaamg_solve from x0 = 0, with its own K-cycle coefficients, outer iteration
+ * and stopping test (|b - A x|_2 <= tol |b|_2, confirmed on the recomputed FP64 residual).
+ * The systems' K-cycles advance together, level step by level step: each step is one launch
+ * over every system that takes it (their levels' rows split into tiles), so the launches of
+ * an outer iteration do not grow with the number of systems.  A system's result does not
+ * depend on which other systems share the call: its tiles, and the order of its inner
+ * products, are a function of its own level sizes and nrhs[s] only.
+ *   B[s], X[s]: float64 [n_s][nrhs[s]] row-major (the columns of row i contiguous), host or
+ *     device pointers; X[s] receives the solutions.
+ *   iters, relres (host): one entry per column, systems in order (nrhs[0] entries for
+ *     system 0, then system 1, ...): outer iterations and the final relative residual.
+ * Returns UAAMG_OK when every column converged within its handle's max_iter, else
+ * UAAMG_ERR_NO_CONVERGENCE with all outputs filled; UAAMG_ERR_INVALID_ARG for a repeated
+ * or null handle or mixed precisions or devices; UAAMG_ERR_UNSUPPORTED for nrhs outside
+ * 1..32 or pre/post != 1.  Runs on a stream of its own, ordered after `stream` and after
+ * each handle's stream (and they after it); it synchronises once per outer iteration.
+ * Each handle keeps a workspace of nrhs[s] columns (as uaamg_solve_many); a handle is used
+ * by this call alone while it runs.  The paper has no batched solve: this is the serving
+ * extension of its K-cycle (Section 4.3) to many systems at once.
+ */
+int uaamg_solve_batch(uaamg_handle* const* handles, int32_t nsys, const int32_t* nrhs,
+                      const double* const* B, double* const* X, double tol, int32_t* iters,
+                      double* relres, void* stream);
+
+/*
+ * uaamg_setup(A[s], p[s], stream) for nsys matrices (p = NULL: defaults for all), run on
+ * `threads` host threads so that the setups of different matrices (each on its handle's own
+ * stream) overlap on the device.  out[s] receives system s's handle, whose caller's stream
+ * is `stream`.  All or nothing: on the first failing status every handle made is freed,
+ * out[] is all NULL and that status is returned.
+ */
+int uaamg_setup_batch(int32_t nsys, const uaamg_csr* A, const uaamg_params* p, int32_t threads,
+                      void* stream, uaamg_handle** out);
+
 /* Releases every device allocation of the handle (stream-ordered on its stream). */
 void uaamg_free(uaamg_handle* h);
 

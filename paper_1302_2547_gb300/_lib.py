@@ -31,6 +31,7 @@ EXPORTS = [
     "uaamg_status_string", "uaamg_aggregate_static", "uaamg_solve_many",
     "uaamg_server_create", "uaamg_server_submit", "uaamg_server_poll", "uaamg_server_wait",
     "uaamg_server_stats", "uaamg_server_destroy", "uaamg_server_cancel",
+    "uaamg_solve_batch", "uaamg_setup_batch",
 ]
 
 
@@ -113,6 +114,8 @@ def lib() -> C.CDLL:
                                              C.POINTER(U64), C.POINTER(U64), C.POINTER(I32)]),
             "uaamg_server_destroy": (None, [P]),
             "uaamg_server_cancel": (C.c_int, [P, U64, C.POINTER(I32)]),
+            "uaamg_solve_batch": (C.c_int, [P, I32, P, P, P, D, P, P, P]),
+            "uaamg_setup_batch": (C.c_int, [I32, P, P, I32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -195,6 +198,53 @@ def uaamg_solve_many(h, B, X, tol: float = 1e-8):
     if st not in (UAAMG_OK, UAAMG_ERR_NO_CONVERGENCE):
         check(st, "uaamg_solve_many")
     return st, it, rr
+
+
+def uaamg_solve_batch(handles, Bs, Xs, tol: float = 1e-8, stream=None):
+    """Solves len(handles) systems together.  Bs[s], Xs[s]: [n_s][nrhs_s] float64 (numpy or
+    torch, host or device; a 1-D array is one right-hand side).  Returns (status,
+    iters list of arrays, relres list of arrays), one array per system."""
+    ns = len(handles)
+    if not (len(Bs) == len(Xs) == ns) or ns < 1:
+        raise ValueError("one B and one X per handle")
+    nr = np.array([1 if len(B.shape) == 1 else int(B.shape[1]) for B in Bs], np.int32)
+    hp = (C.c_void_p * ns)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    bp = (C.c_void_p * ns)(*[_ptr(B)[0] for B in Bs])
+    xp = (C.c_void_p * ns)(*[_ptr(X)[0] for X in Xs])
+    it = np.zeros(int(nr.sum()), np.int32)
+    rr = np.zeros(int(nr.sum()))
+    st = lib().uaamg_solve_batch(hp, ns, nr.ctypes.data, bp, xp, tol, it.ctypes.data,
+                                 rr.ctypes.data, _stream(stream))
+    if st not in (UAAMG_OK, UAAMG_ERR_NO_CONVERGENCE):
+        check(st, "uaamg_solve_batch")
+    off = np.concatenate([[0], np.cumsum(nr)])
+    return st, [it[off[s]:off[s + 1]] for s in range(ns)], [rr[off[s]:off[s + 1]]
+                                                              for s in range(ns)]
+
+
+def uaamg_setup_batch(mats, params=None, threads: int = 8, stream=None):
+    """uaamg_setup of every (rowptr, col, val) in `mats` (host numpy arrays) on `threads`
+    host threads; `params` is one uaamg_params for all or a list of one per matrix.
+    Returns the list of handles."""
+    ns = len(mats)
+    keep = []
+    csr = (uaamg_csr * ns)()
+    for s, (rp, cc, vv) in enumerate(mats):
+        rp = np.ascontiguousarray(rp, np.int32)
+        cc = np.ascontiguousarray(cc, np.int32)
+        vv = np.ascontiguousarray(vv, np.float64)
+        keep += [rp, cc, vv]
+        csr[s] = uaamg_csr(len(rp) - 1, len(cc), rp.ctypes.data, cc.ctypes.data,
+                           vv.ctypes.data, 0)
+    if params is None:
+        pp = None
+    else:
+        plist = params if isinstance(params, (list, tuple)) else [params] * ns
+        pp = (uaamg_params * ns)(*plist)
+    out = (C.c_void_p * ns)()
+    check(lib().uaamg_setup_batch(ns, csr, pp, threads, _stream(stream), out),
+          "uaamg_setup_batch")
+    return [C.c_void_p(out[s]) for s in range(ns)]
 
 
 def uaamg_free(h):

@@ -24,7 +24,9 @@ struct MPrec<double> {
     static const double* minv(const Level& L) { return L.minv64; }
 };
 
-static int ensure_multi(Handle* h, int R) {
+// Workspace of R interleaved columns on every level (kept by the handle; uaamg_solve_batch
+// uses it too).
+int ensure_multi(Handle* h, int R) {
     if (h->multi_R >= R) return UAAMG_OK;
     int st = UAAMG_OK;
     const size_t es = (h->p.precision == UAAMG_MIXED) ? sizeof(float) : sizeof(double);

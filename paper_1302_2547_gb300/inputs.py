@@ -48,29 +48,29 @@ class CSR:
 def laplacian_from_edges(n: int, ei, ej, w, wD=None, name: str = "") -> CSR:
     """CSR of the weighted graph Laplacian of undirected edges (ei[k], ej[k], w[k]), ei != ej,
     each edge listed once, plus the Dirichlet weights wD (length n, zeros allowed)."""
+    from scipy.sparse import csr_matrix
+
     ei = np.asarray(ei, dtype=np.int64)
     ej = np.asarray(ej, dtype=np.int64)
     w = np.asarray(w, dtype=np.float64)
     if np.any(ei == ej):
         raise ValueError("self loops are not edges")
-    diag = np.zeros(n)
-    np.add.at(diag, ei, w)
-    np.add.at(diag, ej, w)
+    # a_ii: the weights of the row's edges added in edge order (ei occurrences, then ej),
+    # then wD
+    diag = np.bincount(np.concatenate([ei, ej]), weights=np.concatenate([w, w]), minlength=n)
     if wD is not None:
-        diag += np.asarray(wD, dtype=np.float64)
+        diag = diag + np.asarray(wD, dtype=np.float64)
     rows = np.concatenate([ei, ej, np.arange(n)])
     cols = np.concatenate([ej, ei, np.arange(n)])
     vals = np.concatenate([-w, -w, diag])
-    order = np.lexsort((cols, rows))
-    rows, cols, vals = rows[order], cols[order], vals[order]
-    if len(rows) > 1 and np.any((rows[1:] == rows[:-1]) & (cols[1:] == cols[:-1])):
-        raise ValueError("duplicate edge")
-    rowptr = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(rowptr, rows + 1, 1)
-    rowptr = np.cumsum(rowptr)
-    if rowptr[-1] >= 2**31:
+    if len(rows) >= 2**31:
         raise ValueError("nnz does not fit int32")
-    return CSR(n, rowptr.astype(np.int32), cols.astype(np.int32), vals, name)
+    M = csr_matrix((vals, (rows, cols)), shape=(n, n))
+    if M.nnz != len(rows):
+        raise ValueError("duplicate edge")
+    M.sort_indices()
+    return CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64),
+               name)
 
 
 def grid2d(nx: int, ny: int | None = None, dirichlet: bool = True, weights=None,
@@ -221,3 +221,36 @@ def laplace3d_128(n: int = 128) -> CSR:
 def rgg_4m(npts: int = 4_000_000) -> CSR:
     """Random geometric graph, 4M points in the unit square, mean degree 8, LCC, one pin."""
     return rgg(npts, 8.0, seed=MATRIX_SEED + 2, name=f"rgg_{npts}_deg8")
+
+
+def _batch_member(args):
+    """System k of batch_mix (a separate function so that a process pool can build it)."""
+    k, n, seed = args
+    if k % 2 == 0:
+        side = max(2, int(round(math.sqrt(n))))
+        return grid2d(side, side, name=f"batch{k}_grid2d_{side}")
+    return rgg(int(n), 8.0, seed=seed + k, name=f"batch{k}_rgg_{int(n)}")
+
+
+def batch_mix_sizes(nsys: int = 512, nmin: int = 1024, nmax: int = 262144,
+                    seed: int = MATRIX_SEED + 4) -> np.ndarray:
+    """Requested sizes of batch_mix: log-uniform in [nmin, nmax]."""
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(math.log(nmin), math.log(nmax), nsys)).astype(np.int64)
+
+
+def batch_mix(nsys: int = 512, nmin: int = 1024, nmax: int = 262144,
+              seed: int = MATRIX_SEED + 4, processes: int = 0) -> list:
+    """The batched workload: nsys independent systems with sizes log-uniform in
+    [nmin, nmax]; even-numbered systems are 2D 5-point Dirichlet grids of side
+    round(sqrt(n)) (unit weights), odd-numbered ones random geometric graphs of mean degree 8
+    (largest component, one pinned vertex).  processes > 1 builds them in that many spawned
+    processes (the systems do not depend on it)."""
+    sizes = batch_mix_sizes(nsys, nmin, nmax, seed)
+    jobs = [(k, int(n), seed) for k, n in enumerate(sizes)]
+    if processes > 1:
+        import multiprocessing as mp
+
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.map(_batch_member, jobs, chunksize=4)
+    return [_batch_member(j) for j in jobs]
