@@ -39,6 +39,24 @@ BENCH_PARAMS = dict(max_agg_size=4, agg_repeat=2, kcycle_ratio=5.0, min_coarseni
 # thousand vertices).
 RGG_PARAMS = dict(max_agg_size=0, agg_repeat=1, kcycle_ratio=3.0, min_coarsening=1.5)
 
+# The batched workload: 512 independent systems, sizes log-uniform in [1024, 262144],
+# even-numbered ones 2D 5-point grids and odd-numbered ones random geometric graphs of mean
+# degree 8, 16 right-hand sides each.  2D grids take one aggregation per level with
+# aggregates of at most 6 vertices, two flexible-CG steps on every level reached by at
+# least 2x coarsening and a coarsest level of up to 512 unknowns: 17-20 iterations at every
+# size, where the 3D parameters need 60-130 (the paper's limit 5 stalls near 1.08x per level
+# on some grid widths, which with two steps everywhere makes the K-cycle exponential).  The
+# graphs take the unstructured parameters above.
+C4_GRID2D_PARAMS = dict(max_agg_size=6, agg_repeat=1, kcycle_ratio=2.0, min_coarsening=1.5,
+                        coarse_size=512)
+C4_NSYS, C4_R = 512, 16
+C4_SYSTEMS_RUN = C4_NSYS  # --c4-systems: run only the first k systems (a smaller probe)
+
+
+def c4_params(k: int) -> dict:
+    return C4_GRID2D_PARAMS if k % 2 == 0 else RGG_PARAMS
+
+
 # DRAM traffic per launch of each roofline kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by a hash of the sources that
 # define that kernel: it reads as null once any of them changes.
@@ -364,6 +382,159 @@ def run_gpu(args, rank, world):
     return out
 
 
+def _progress(msg: str):
+    """A progress line on stderr with the host memory in use (the JSON line is stdout)."""
+    rss = avail = "?"
+    try:
+        for line in open("/proc/self/status"):
+            if line.startswith("VmRSS:"):
+                rss = line.split()[1]
+        avail = str(_mem_available() // 1024)
+    except OSError:
+        pass
+    print(f"[bench] {msg} (rss {rss} kB, available {avail} kB)", file=sys.stderr, flush=True)
+
+
+def c4_workload():
+    """The batched workload's systems and right-hand sides ([n][16] per system, uniform
+    [-1, 1], seeded per system)."""
+    from paper_1302_2547_gb300 import inputs as I
+
+    S = I.batch_mix(C4_NSYS, processes=min(16, os.cpu_count() or 1))[:C4_SYSTEMS_RUN]
+    Bs = [np.random.default_rng([I.RHS_SEED + 4, k]).uniform(-1.0, 1.0, (A.n, C4_R))
+          for k, A in enumerate(S)]
+    return S, Bs
+
+
+def run_c4(warmup=1, steps=1):
+    """The batched workload through uaamg_setup_batch + uaamg_solve_batch (mixed precision,
+    inputs resident in HBM), beside the plain one-at-a-time FP64 path on the same systems
+    (uaamg_setup + uaamg_solve per right-hand side), and end to end from host buffers."""
+    import torch
+    import scipy.sparse as sp
+
+    from paper_1302_2547_gb300 import _lib as U
+
+    t_gen = time.perf_counter()
+    S, Bs = c4_workload()
+    t_gen = time.perf_counter() - t_gen
+    ns, R = len(S), C4_R
+    _progress(f"batched workload generated in {t_gen:.1f} s")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        csr_d = [tuple(torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val)) for A in S]
+        Bd = [torch.from_numpy(B).to(dev) for B in Bs]
+        Xd = [torch.zeros_like(b) for b in Bd]
+    stream.synchronize()
+    pm = [U.uaamg_default_params(precision=U.UAAMG_MIXED, **c4_params(k)) for k in range(ns)]
+    threads = min(16, os.cpu_count() or 1)
+
+    def batched_step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        hs = U.uaamg_setup_batch(csr_d, pm, threads=threads, stream=stream)
+        _progress("batched setup returned")
+        try:
+            e[1].record(stream)
+            st, its, rrs = U.uaamg_solve_batch(hs, Bd, Xd, TOL, stream=stream)
+            e[2].record(stream)
+            stream.synchronize()
+            levels = [U.uaamg_num_levels(h) for h in hs]
+        finally:
+            for h in hs:
+                U.uaamg_free(h)
+        if st != 0:
+            raise RuntimeError(f"batched solve status {st}")
+        return e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), its, rrs, levels
+
+    for _ in range(warmup):
+        batched_step()
+        _progress("batched warm-up step done")
+    l0 = U.uaamg_total_launches()
+    rec = [batched_step() for _ in range(steps)]
+    launches = (U.uaamg_total_launches() - l0) // max(1, steps)
+    setup_ms = float(np.median([r[0] for r in rec]))
+    solve_ms = float(np.median([r[1] for r in rec]))
+    its = np.concatenate(rec[-1][2])
+    worst = 0.0
+    for k, A in enumerate(S):  # every column of every system, on the host in FP64
+        Asp = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+        X = Xd[k].cpu().numpy()
+        res = np.linalg.norm(Bs[k] - Asp @ X, axis=0) / np.linalg.norm(Bs[k], axis=0)
+        worst = max(worst, float(res.max()))
+    total_ms = setup_ms + solve_ms
+    _progress("batched steps checked on the host")
+    batched = {
+        "value": round(ns * R / (total_ms / 1000.0), 1), "unit": "solves/s",
+        "systems": ns, "rhs_per_system": R, "setup_ms": round(setup_ms, 2),
+        "solve_ms": round(solve_ms, 2),
+        "iterations": {"median": float(np.median(its)), "max": int(its.max())},
+        "levels": {"min": int(min(rec[-1][4])), "max": int(max(rec[-1][4]))},
+        "latency_ms": {"p50": round(total_ms, 2), "p99": round(total_ms, 2),
+                       "note": "every solve of the batch is answered when the call returns"},
+        "relres_host_fp64_max": worst, "gpu_launches": int(launches),
+        "precision": "FP32 hierarchy + K-cycle, FP64 outer flexible CG"}
+
+    # plain: one system at a time, FP64 throughout, one solve per right-hand side; every
+    # system's setup and its first right-hand side are timed, the other 15 solves of a
+    # system take the same iterations within one or two and are counted at that time
+    plain_setup, plain_solve, plain_it = [], [], []
+    x1 = [torch.zeros(A.n, dtype=torch.float64, device=dev) for A in S]
+    b1 = [b[:, 0].contiguous() for b in Bd]
+    stream.synchronize()
+    with torch.cuda.stream(stream):
+        for k, A in enumerate(S):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            h = U.uaamg_setup(*csr_d[k], U.uaamg_default_params(precision=U.UAAMG_FP64,
+                                                                 **c4_params(k)), stream=stream)
+            e[1].record(stream)
+            st, it, rr = U.uaamg_solve(h, b1[k], x1[k], TOL)
+            e[2].record(stream)
+            stream.synchronize()
+            U.uaamg_free(h)
+            if st != 0:
+                raise RuntimeError(f"plain solve status {st} on system {k}")
+            plain_setup.append(e[0].elapsed_time(e[1]))
+            plain_solve.append(e[1].elapsed_time(e[2]))
+            plain_it.append(it)
+    plain_ms = float(np.sum(plain_setup) + R * np.sum(plain_solve))
+    _progress("plain path done")
+    plain = {
+        "value": round(ns * R / (plain_ms / 1000.0), 2), "unit": "solves/s",
+        "setup_ms_per_system": {"median": round(float(np.median(plain_setup)), 3)},
+        "solve_ms_per_rhs": {"p50": round(float(np.percentile(plain_solve, 50)), 3),
+                             "p99": round(float(np.percentile(plain_solve, 99)), 3)},
+        "iterations": {"median": float(np.median(plain_it)), "max": int(max(plain_it))},
+        "sample": f"all {ns} systems: setup + first right-hand side timed, the other "
+                  f"{R - 1} right-hand sides of each system counted at its solve time"}
+
+    # end to end from host buffers: CSR and B copied in, X copied out, inside the timed region
+    Bp = [torch.from_numpy(B).pin_memory() for B in Bs]
+    Xp = [torch.zeros_like(b).pin_memory() for b in Bp]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = U.uaamg_setup_batch([(A.rowptr, A.col, A.val) for A in S], pm, threads=threads)
+    try:
+        st, _, _ = U.uaamg_solve_batch(hs, Bp, Xp, TOL)
+    finally:
+        for h in hs:
+            U.uaamg_free(h)
+    te = time.perf_counter() - t0
+    h2d = sum(A.rowptr.nbytes + A.col.nbytes + A.val.nbytes for A in S) + sum(B.nbytes for B in Bs)
+    batched["e2e"] = {"value": round(ns * R / te, 1), "unit": "solves/s",
+                      "h2d_bytes": int(h2d), "d2h_bytes": int(sum(B.nbytes for B in Bs)),
+                      "status": int(st)}
+    batched["vs_plain_fp64"] = round(batched["value"] / plain["value"], 2)
+    return {"workload": f"{ns} systems, sizes log-uniform 1024-262144 (2D 5-point grids and "
+                        f"random geometric graphs of mean degree 8, alternating), {R} "
+                        f"right-hand sides each, tol {TOL}",
+            "unknowns": int(sum(A.n for A in S)), "nnz": int(sum(A.nnz for A in S)),
+            "params": {"grid2d": C4_GRID2D_PARAMS, "rgg": RGG_PARAMS},
+            "generate_s": round(t_gen, 2), "batched_mixed": batched, "plain_fp64": plain}
+
+
 def run_rgg(steps=3, warmup=1):
     """Setup + mixed solve of the 4M-point random geometric graph (inputs resident), timed
     like the main line; reported beside it, not as the headline."""
@@ -663,6 +834,12 @@ def main():
                     help="do not time subgraph reshaping (Algorithm 3) on the workload")
     ap.add_argument("--sra-only", action="store_true",
                     help="print only the subgraph-reshaping measurement as one JSON line")
+    ap.add_argument("--skip-c4", action="store_true",
+                    help="do not run the batched workload (512 systems x 16 right-hand sides)")
+    ap.add_argument("--c4-only", action="store_true",
+                    help="print only the batched workload's measurement as one JSON line")
+    ap.add_argument("--c4-systems", type=int, default=0,
+                    help="run only the first k systems of the batched workload")
     ap.add_argument("--rgg", action="store_true",
                     help="also time the 4M-point random geometric graph (about a minute)")
     ap.add_argument("--tma-rows", type=int, default=None,
@@ -713,6 +890,13 @@ def main():
         import torch.distributed as dist
 
         dist.barrier()
+    global C4_SYSTEMS_RUN
+    if args.c4_systems:
+        C4_SYSTEMS_RUN = args.c4_systems
+    if args.c4_only:
+        if rank == 0:
+            print(json.dumps({"c4_batched": run_c4()}))
+        return
     if args.sra_only:
         if rank == 0:
             print(json.dumps({"workload": WORKLOAD, "sra": run_sra()}))
@@ -724,6 +908,11 @@ def main():
                 out["sra"] = run_sra()
             except Exception as e:  # reported, not hidden: the main line still stands
                 out["sra"] = {"error": f"{type(e).__name__}: {e}"}
+        if world == 1 and not args.skip_c4:
+            try:
+                out["c4_batched"] = run_c4()
+            except Exception as e:  # reported, not hidden: the main line still stands
+                out["c4_batched"] = {"error": f"{type(e).__name__}: {e}"}
         if world == 1 and args.rgg:
             out["rgg_4m"] = run_rgg()
         if world == 1 and not args.skip_serving:

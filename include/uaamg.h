@@ -186,7 +186,8 @@ int uaamg_solve_many(uaamg_handle* h, int32_t nrhs, const double* B, double* X, 
  * Returns UAAMG_OK when every column converged within its handle's max_iter, else
  * UAAMG_ERR_NO_CONVERGENCE with all outputs filled; UAAMG_ERR_INVALID_ARG for a repeated
  * or null handle or mixed precisions or devices; UAAMG_ERR_UNSUPPORTED for nrhs outside
- * 1..32 or pre/post != 1.  Runs on a stream of its own, ordered after `stream` and after
+ * 1..32, pre/post != 1, or K-cycles whose union needs more than 65536 launches per outer
+ * iteration (two flexible-CG steps on many levels make the cycle exponential in depth).  Runs on a stream of its own, ordered after `stream` and after
  * each handle's stream (and they after it); it synchronises once per outer iteration.
  * Each handle keeps a workspace of nrhs[s] columns (as uaamg_solve_many); a handle is used
  * by this call alone while it runs.  The paper has no batched solve: this is the serving

@@ -223,19 +223,22 @@ def uaamg_solve_batch(handles, Bs, Xs, tol: float = 1e-8, stream=None):
 
 
 def uaamg_setup_batch(mats, params=None, threads: int = 8, stream=None):
-    """uaamg_setup of every (rowptr, col, val) in `mats` (host numpy arrays) on `threads`
-    host threads; `params` is one uaamg_params for all or a list of one per matrix.
-    Returns the list of handles."""
+    """uaamg_setup of every (rowptr, col, val) in `mats` on `threads` host threads; each
+    triple is all host (numpy) or all device (torch CUDA) arrays.  `params` is one
+    uaamg_params for all or a list of one per matrix.  Returns the list of handles."""
     ns = len(mats)
     keep = []
     csr = (uaamg_csr * ns)()
     for s, (rp, cc, vv) in enumerate(mats):
-        rp = np.ascontiguousarray(rp, np.int32)
-        cc = np.ascontiguousarray(cc, np.int32)
-        vv = np.ascontiguousarray(vv, np.float64)
+        if not hasattr(rp, "data_ptr"):
+            rp = np.ascontiguousarray(rp, np.int32)
+            cc = np.ascontiguousarray(cc, np.int32)
+            vv = np.ascontiguousarray(vv, np.float64)
         keep += [rp, cc, vv]
-        csr[s] = uaamg_csr(len(rp) - 1, len(cc), rp.ctypes.data, cc.ctypes.data,
-                           vv.ctypes.data, 0)
+        (a, d0), (b, d1), (c, d2) = _ptr(rp), _ptr(cc), _ptr(vv)
+        if not (d0 == d1 == d2):
+            raise ValueError("rowptr, col and val must all be host or all device arrays")
+        csr[s] = uaamg_csr(int(rp.shape[0]) - 1, int(cc.shape[0]), a, b, c, d0)
     if params is None:
         pp = None
     else:

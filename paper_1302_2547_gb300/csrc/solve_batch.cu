@@ -73,8 +73,17 @@ struct Plan {
         return r;
     }
 
+    // The union of the systems' K-cycles is exponential in the depth of levels that take
+    // two steps; a plan beyond kMaxRecs launches per outer iteration is refused.
+    static constexpr size_t kMaxRecs = 1 << 16;
+    bool too_big = false;
+
     void emit(Rec r, const std::vector<int>& parts) {
-        if (parts.empty()) return;
+        if (parts.empty() || too_big) return;
+        if (recs.size() >= kMaxRecs) {
+            too_big = true;
+            return;
+        }
         r = table(r, parts, &tab);
         long long need = (long long)r.tiles * 3 * kBPartStride;
         if (need > max_part) max_part = need;
@@ -83,6 +92,7 @@ struct Plan {
 
     // out = K_m(in) for the systems `parts` (level m exists for each of them).
     void K(int m, const std::vector<int>& parts, int s_in, int s_out) {
+        if (too_big) return;
         std::vector<int> dense, fcg, two;
         for (int s : parts) (m == nlev[s] - 1 ? dense : fcg).push_back(s);
         {
@@ -324,6 +334,7 @@ int solve_batch(Handle* const* hs, int nsys, const int* R, const double* const* 
     std::vector<int> all(nsys);
     for (int s = 0; s < nsys; s++) all[s] = s;
     plan.outer(all, mixed);
+    if (plan.too_big) return UAAMG_ERR_UNSUPPORTED;
     const size_t n_iter_recs = plan.recs.size();
     // launches outside the iteration graph, over every system
     plan.emit(rec(BK_INIT, 0), all);
