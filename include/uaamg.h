@@ -280,10 +280,14 @@ const char* uaamg_status_string(int status);
  * are freed to admit new ones within budget_bytes (0 = no budget; the budget is applied
  * library-wide with uaamg_set_memory_budget while the server lives).  A request whose
  * estimated hierarchy cannot fit the budget is answered with UAAMG_ERR_BUDGET; one that
- * fits after eviction waits until memory frees.  Continuous batching: when a worker takes a
- * request it also takes every queued request for the same matrix and tolerance (up to
- * max_batch <= 32) and solves them together with uaamg_solve_many.  Each answer is the same
- * algorithm as uaamg_solve on that matrix.
+ * fits after eviction waits until memory frees.  Continuous batching: a free worker takes,
+ * in arrival order, every queued request whose matrix no other worker is using and whose
+ * tolerance equals the oldest one's, up to max_batch <= 32 requests; requests for one matrix
+ * become the columns of one system, and different matrices the systems of one
+ * uaamg_solve_batch call (one system: uaamg_solve or uaamg_solve_many), so their K-cycles
+ * advance level step by level step in shared launches.  Requests that arrive meanwhile wait
+ * for the next free worker.  Each answer is the same algorithm as uaamg_solve on that
+ * matrix (pre = post = 1; other sweep counts batch only requests of one matrix).
  */
 typedef struct uaamg_server uaamg_server;
 int uaamg_server_create(const uaamg_params* p, uint64_t budget_bytes, int32_t workers,

@@ -191,6 +191,8 @@ template <typename T>
 T* dalloc(Handle* h, size_t count, int* status, bool temp = false) {
     return static_cast<T*>(dalloc_bytes(h, sizeof(T) * (count ? count : 1), status, temp));
 }
+// Releases one allocation of the handle made with dalloc_bytes(h, bytes) (stream-ordered).
+void dfree_one(Handle* h, void* ptr, size_t bytes);
 void dfree_temps(Handle* h);
 void dfree_all(Handle* h);
 void count_launch(Handle* h, long long k = 1);

@@ -12,6 +12,8 @@
 
 namespace uaamg {
 
+constexpr int kBGather = 8;  // row entries whose loads a thread issues together
+
 // The tile of this block: its system (binary search over the segments' first tiles), the
 // tile's index within the system and the system's tile count at this launch.
 struct BTile {
@@ -152,14 +154,32 @@ __global__ void __launch_bounds__(kThreads) kb_row(BArgs a) {
         const size_t o = (size_t)i * R + lr;
         T acc = T(0);
         const int k1 = rowptr[i + 1];
-        for (int k = rowptr[i]; k < k1; k++) {
-            const int j = col[k];
-            const size_t oj = (size_t)j * R + lr;
-            T xj;
-            if constexpr (MODE == RB_PRE1) xj = mul_rn(minv[j], r[oj]);
-            else if constexpr (MODE == RB_PROSMOOTH) xj = add_rn(x[oj], e[(size_t)agg[j] * R + lr]);
-            else xj = x[oj];
-            acc = fma_rn(val[k], xj, acc);
+        // kBGather entries at a time: their columns and values, then their vector entries,
+        // are loaded before the first is used; the sum keeps the stored order
+        for (int k = rowptr[i]; k < k1; k += kBGather) {
+            int jj[kBGather];
+            T vv[kBGather], xg[kBGather];
+#pragma unroll
+            for (int u = 0; u < kBGather; u++) {
+                const bool in = k + u < k1;
+                jj[u] = in ? col[k + u] : 0;
+                vv[u] = in ? val[k + u] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kBGather; u++) {
+                const size_t oj = (size_t)jj[u] * R + lr;
+                T xj = T(0);
+                if (k + u < k1) {
+                    if constexpr (MODE == RB_PRE1) xj = mul_rn(minv[jj[u]], r[oj]);
+                    else if constexpr (MODE == RB_PROSMOOTH)
+                        xj = add_rn(x[oj], e[(size_t)agg[jj[u]] * R + lr]);
+                    else xj = x[oj];
+                }
+                xg[u] = xj;
+            }
+#pragma unroll
+            for (int u = 0; u < kBGather; u++)
+                if (k + u < k1) acc = fma_rn(vv[u], xg[u], acc);
         }
         if constexpr (MODE == RB_PRE1) {
             y[o] = mul_rn(minv[i], r[o]);

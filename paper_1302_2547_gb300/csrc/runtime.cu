@@ -71,6 +71,20 @@ void* dalloc_bytes(Handle* h, size_t bytes, int* status, bool temp) {
     return ptr;
 }
 
+void dfree_one(Handle* h, void* ptr, size_t bytes) {
+    if (!ptr) return;
+    bytes = (bytes + 32 + 255) & ~(size_t)255;  // as dalloc_bytes rounded it
+    for (size_t k = 0; k < h->allocs.size(); k++) {
+        if (h->allocs[k] != ptr) continue;
+        h->allocs[k] = h->allocs.back();
+        h->allocs.pop_back();
+        cudaFreeAsync(ptr, h->work);
+        g_bytes.fetch_sub(bytes);
+        h->bytes -= bytes;
+        return;
+    }
+}
+
 void dfree_temps(Handle* h) {
     for (auto& t : h->temps) {
         cudaFreeAsync(t.first, h->work);

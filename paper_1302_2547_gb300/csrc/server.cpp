@@ -1,9 +1,11 @@
 // server.cpp -- a solve service on one GPU: requests (matrix, right-hand side, tolerance)
 // are queued, admitted against a device-memory budget, served from a cache of device-
-// resident hierarchies keyed by the matrix, and batched: queued requests for the same
-// matrix are solved together with uaamg_solve_many, and worker threads with their own
-// CUDA streams keep several solves in flight.  Host-side orchestration only: every compute
-// step is a libuaamg kernel.
+// resident hierarchies keyed by the matrix, and batched: a worker takes the queued requests
+// of every idle matrix at once, requests for one matrix as the columns of one system and
+// different matrices as the systems of one uaamg_solve_batch call (their K-cycles advance
+// level step by level step together), and worker threads with their own CUDA streams keep
+// several batches in flight.  Host-side orchestration only: every compute step is a
+// libuaamg kernel.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -108,134 +110,203 @@ struct uaamg_server {
 };
 
 // Device bytes a hierarchy of this matrix may take (level 0 plus coarse levels, smoother
-// data, workspace and setup scratch): used for admission before setup runs.
-static uint64_t estimate_bytes(const Matrix& A, int max_batch) {
+// data, setup scratch, and the solve workspace of up to `cols` right-hand sides): used for
+// admission before setup runs.
+static uint64_t estimate_bytes(const Matrix& A, int cols) {
     const uint64_t n = (uint64_t)A.n, z = (uint64_t)A.nnz;
-    return 2 * (16 * z + 120 * n) + (uint64_t)max_batch * n * 48 + (64ULL << 20);
+    return 2 * (16 * z + 120 * n) + (uint64_t)cols * n * 96 + (64ULL << 20);
 }
 
+namespace {
+// One system of a batch: the requests for one matrix (its columns) and its hierarchy.
+struct Group {
+    std::vector<std::shared_ptr<Request>> reqs;
+    CacheEntry* entry = nullptr;
+    bool need_setup = false;
+    int status = UAAMG_OK;
+};
+}  // namespace
+
 void uaamg_server::worker_main(int wid) {
+    (void)wid;
     cudaSetDevice(device);
     cudaStream_t stream = nullptr;
     cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    // the many-system solve needs one sweep before and after the coarse correction
+    const bool cross = params.pre == 1 && params.post == 1;
+    const int cols = std::min(max_batch, 32);
     while (true) {
-        std::vector<std::shared_ptr<Request>> batch;
-        CacheEntry* entry = nullptr;
-        bool need_setup = false;
+        std::vector<Group> groups;
+        int taken = 0;
         {
             std::unique_lock<std::mutex> lk(mu);
-            // the oldest request whose matrix is not being set up or solved by another
-            // worker (a handle serves one thread at a time; requests for a busy matrix keep
-            // queueing and are batched when it frees)
-            auto pick = [&]() {
-                for (auto it = queue.begin(); it != queue.end(); ++it) {
-                    bool busy = false;
-                    for (auto& e : cache)
-                        if (e.key == (*it)->A->key && e.users > 0) busy = true;
-                    if (!busy) return it;
-                }
-                return queue.end();
+            // a handle serves one thread at a time: requests for a matrix another worker
+            // is setting up or solving wait, and join a later batch
+            auto idle = [&](uint64_t key) {
+                for (auto& e : cache)
+                    if (e.key == key && e.users > 0) return false;
+                return true;
             };
-            auto sel = queue.end();
             cv_work.wait(lk, [&] {
                 if (stopping && queue.empty()) return true;
-                sel = pick();
-                return sel != queue.end();
+                for (auto& q : queue)
+                    if (idle(q->A->key)) return true;
+                return false;
             });
             if (stopping && queue.empty()) break;
-            // continuous batching: that request plus every queued request for the same matrix
-            // and tolerance, up to max_batch
-            auto first = *sel;
-            queue.erase(sel);
-            batch.push_back(first);
-            for (auto it = queue.begin(); it != queue.end() && (int)batch.size() < max_batch;) {
-                if ((*it)->A->key == first->A->key && (*it)->tol == first->tol) {
-                    batch.push_back(*it);
-                    it = queue.erase(it);
-                } else {
+            // continuous batching: in arrival order, every queued request of an idle matrix
+            // with the first one's tolerance, up to max_batch requests; requests for one
+            // matrix become the columns of one system, different matrices different systems
+            // of one uaamg_solve_batch call
+            double tol = 0.0;
+            bool rejected = false, wait_memory = false;
+            uint64_t reserve = 0;  // bytes of the hierarchies this batch sets up
+            std::unordered_map<uint64_t, size_t> gi;
+            for (auto it = queue.begin(); it != queue.end() && taken < max_batch;) {
+                std::shared_ptr<Request> q = *it;
+                const uint64_t key = q->A->key;
+                auto f = gi.find(key);
+                const bool joins = f != gi.end();
+                if ((!joins && !idle(key)) || (taken > 0 && q->tol != tol) ||
+                    (joins && (int)groups[f->second].reqs.size() >= cols) ||
+                    (!cross && taken > 0 && !joins)) {
                     ++it;
+                    continue;
                 }
-            }
-            entry = find(first->A->key);
-            if (entry) {
-                entry->users++;
-                n_hits += batch.size();
-                for (auto& r : batch) r->cache_hit = 1;
-            } else {
-                const uint64_t need = estimate_bytes(*first->A, max_batch);
-                if (budget && need > budget) {  // can never fit: reject
-                    for (auto& r : batch) {
-                        r->status = UAAMG_ERR_BUDGET;
-                        r->done = true;
+                if (!joins) {  // a new system: cached, or set up by this worker within budget
+                    Group g;
+                    g.entry = find(key);
+                    if (!g.entry) {
+                        const uint64_t need = estimate_bytes(*q->A, cols);
+                        if (budget && need > budget) {  // can never fit: reject
+                            q->status = UAAMG_ERR_BUDGET;
+                            q->done = true;
+                            n_rejected++;
+                            rejected = true;
+                            it = queue.erase(it);
+                            continue;
+                        }
+                        if (!make_room(reserve + need)) {
+                            if (taken == 0) wait_memory = true;
+                            if (taken == 0) break;
+                            ++it;
+                            continue;
+                        }
+                        reserve += need;
+                        cache.push_front(CacheEntry{key, nullptr, need, 0, nullptr});
+                        g.entry = &cache.front();
+                        g.need_setup = true;
                     }
-                    n_rejected += batch.size();
-                    cv_done.notify_all();
-                    cv_work.notify_all();
-                    continue;
+                    g.entry->users++;
+                    f = gi.emplace(key, groups.size()).first;
+                    groups.push_back(std::move(g));
                 }
-                if (!make_room(need)) {  // wait for memory: put the batch back at the front
-                    for (auto it = batch.rbegin(); it != batch.rend(); ++it) queue.push_front(*it);
-                    cv_done.wait_for(lk, std::chrono::milliseconds(2));
-                    continue;
+                Group& g = groups[f->second];
+                if (!g.need_setup) {
+                    q->cache_hit = 1;
+                    n_hits++;
                 }
-                cache.push_front(CacheEntry{first->A->key, nullptr, need, 1, nullptr});
-                entry = &cache.front();
-                need_setup = true;
+                g.reqs.push_back(q);
+                tol = q->tol;
+                taken++;
+                it = queue.erase(it);
+            }
+            if (rejected) cv_done.notify_all();
+            if (groups.empty()) {
+                if (wait_memory) cv_done.wait_for(lk, std::chrono::milliseconds(2));
+                continue;
             }
         }
-        const Matrix& A = *batch[0]->A;
-        int st = UAAMG_OK;
-        if (need_setup) {
+        // set up the matrices this batch brings (outside the lock)
+        for (Group& g : groups) {
+            if (!g.need_setup) continue;
+            const Matrix& A = *g.reqs[0]->A;
             uaamg_csr csr{A.n, A.nnz, A.rowptr.data(), A.col.data(), A.val.data(), 0};
             uaamg_handle* h = nullptr;
-            st = uaamg_setup(&csr, &params, stream, &h);
+            g.status = uaamg_setup(&csr, &params, stream, &h);
             std::lock_guard<std::mutex> lk(mu);
             n_setups++;
-            if (st != UAAMG_OK) {
+            if (g.status != UAAMG_OK) {
                 for (auto it = cache.begin(); it != cache.end(); ++it)
-                    if (&*it == entry) {
+                    if (&*it == g.entry) {
                         cache.erase(it);
                         break;
                     }
-                entry = nullptr;
+                g.entry = nullptr;
             } else {
-                entry->h = h;
+                g.entry->h = h;
             }
         }
-        const int R = (int)batch.size();
-        std::vector<int32_t> its(R, 0);
-        std::vector<double> rr(R, 0.0);
-        std::vector<double> X((size_t)A.n * R, 0.0);
-        if (st == UAAMG_OK) {
-            if (R == 1) {
-                st = uaamg_solve(entry->h, batch[0]->b.data(), X.data(), batch[0]->tol, 0, &its[0],
-                                 &rr[0]);
-            } else {
-                std::vector<double> B((size_t)A.n * R);
-                for (int r = 0; r < R; r++)
-                    for (int i = 0; i < A.n; i++) B[(size_t)i * R + r] = batch[r]->b[i];
-                st = uaamg_solve_many(entry->h, R, B.data(), X.data(), batch[0]->tol, its.data(),
-                                      rr.data());
+        // the systems whose setup succeeded, solved together
+        std::vector<Group*> live;
+        for (Group& g : groups)
+            if (g.status == UAAMG_OK) live.push_back(&g);
+        const int ns = (int)live.size();
+        std::vector<int32_t> nr(ns);
+        std::vector<std::vector<double>> B(ns), X(ns);
+        std::vector<int32_t> its;
+        std::vector<double> rr;
+        int st = UAAMG_OK;
+        for (int s = 0; s < ns; s++) {
+            const Group& g = *live[s];
+            const int R = (int)g.reqs.size(), n = g.reqs[0]->A->n;
+            nr[s] = R;
+            B[s].resize((size_t)n * R);
+            X[s].assign((size_t)n * R, 0.0);
+            for (int r = 0; r < R; r++)
+                for (int i = 0; i < n; i++) B[s][(size_t)i * R + r] = g.reqs[r]->b[i];
+        }
+        size_t ncol = 0;
+        for (int s = 0; s < ns; s++) ncol += nr[s];
+        its.assign(ncol, 0);
+        rr.assign(ncol, 0.0);
+        const double tol = taken ? groups[0].reqs[0]->tol : 1e-8;
+        if (ns == 1 && nr[0] == 1) {
+            st = uaamg_solve(live[0]->entry->h, B[0].data(), X[0].data(), tol, 0, &its[0], &rr[0]);
+        } else if (ns == 1) {
+            st = uaamg_solve_many(live[0]->entry->h, nr[0], B[0].data(), X[0].data(), tol,
+                                  its.data(), rr.data());
+        } else if (ns > 1) {
+            std::vector<uaamg_handle*> hs(ns);
+            std::vector<const double*> bp(ns);
+            std::vector<double*> xp(ns);
+            for (int s = 0; s < ns; s++) {
+                hs[s] = live[s]->entry->h;
+                bp[s] = B[s].data();
+                xp[s] = X[s].data();
             }
+            st = uaamg_solve_batch(hs.data(), ns, nr.data(), bp.data(), xp.data(), tol,
+                                   its.data(), rr.data(), stream);
         }
         const auto t_end = Clock::now();
         std::lock_guard<std::mutex> lk(mu);
-        if (entry) entry->users--;
-        for (int r = 0; r < R; r++) {
-            Request& q = *batch[r];
-            q.x.resize(A.n);
-            for (int i = 0; i < A.n; i++) q.x[i] = X[(size_t)i * R + r];
-            q.status = (st == UAAMG_ERR_NO_CONVERGENCE) ? (rr[r] <= q.tol ? UAAMG_OK : st) : st;
-            q.iters = its[r];
-            q.relres = rr[r];
-            q.batch = R;
-            q.latency_ms = std::chrono::duration<double, std::milli>(t_end - q.t_submit).count();
-            q.done = true;
+        size_t c = 0;
+        for (int s = 0; s < ns; s++) {
+            Group& g = *live[s];
+            const int R = nr[s], n = g.reqs[0]->A->n;
+            for (int r = 0; r < R; r++, c++) {
+                Request& q = *g.reqs[r];
+                q.x.resize(n);
+                for (int i = 0; i < n; i++) q.x[i] = X[s][(size_t)i * R + r];
+                q.status = (st == UAAMG_ERR_NO_CONVERGENCE) ? (rr[c] <= q.tol ? UAAMG_OK : st) : st;
+                q.iters = its[c];
+                q.relres = rr[c];
+            }
         }
-        n_done += R;
+        for (Group& g : groups) {
+            if (g.entry) g.entry->users--;
+            for (auto& q : g.reqs) {
+                if (g.status != UAAMG_OK) q->status = g.status;
+                q->batch = taken;
+                q->latency_ms =
+                    std::chrono::duration<double, std::milli>(t_end - q->t_submit).count();
+                q->done = true;
+            }
+        }
+        n_done += taken;
         n_batches++;
         cv_done.notify_all();
-        cv_work.notify_all();  // a matrix became free: queued requests for it can run
+        cv_work.notify_all();  // matrices became free: queued requests for them can run
     }
     cudaStreamDestroy(stream);
 }

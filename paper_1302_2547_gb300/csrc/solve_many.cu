@@ -31,6 +31,25 @@ int ensure_multi(Handle* h, int R) {
     int st = UAAMG_OK;
     const size_t es = (h->p.precision == UAAMG_MIXED) ? sizeof(float) : sizeof(double);
     const int n0 = h->lev[0].n;
+    if (h->mgraph) {  // its nodes name the buffers released below
+        cudaGraphExecDestroy(h->mgraph);
+        h->mgraph = nullptr;
+        h->mgraph_R = 0;
+    }
+    if (h->multi_R > 0) {  // the narrower workspace goes (after the work queued on it)
+        const int R0 = h->multi_R;
+        for (int l = 0; l < h->nlev; l++) {
+            MultiLevel& M = h->mlev[l];
+            const size_t bytes = es * (size_t)h->lev[l].n * R0;
+            void* vs[] = {M.rhs, M.out, M.w, M.s, M.c1, M.v1, M.rt, M.c2, M.v2};
+            for (void* v : vs) dfree_one(h, v, bytes);
+            dfree_one(h, M.sc, sizeof(double) * 7 * (size_t)R0);
+        }
+        double* os[] = {h->mb, h->mx, h->mr, h->mp, h->mq};
+        for (double* v : os) dfree_one(h, v, sizeof(double) * (size_t)n0 * R0);
+        dfree_one(h, h->mos, sizeof(double) * 8 * (size_t)R0);
+        h->multi_R = 0;
+    }
     for (int l = 0; l < h->nlev; l++) {
         Level& L = h->lev[l];
         MultiLevel& M = h->mlev[l];
@@ -64,13 +83,12 @@ int ensure_multi(Handle* h, int R) {
         h->partials_cap = pneed;
     }
     if (st) return st;
-    if (h->mos_host) cudaFreeHost(h->mos_host);
-    if (cudaMallocHost(&h->mos_host, sizeof(double) * 8 * R) != cudaSuccess) return UAAMG_ERR_OOM;
-    if (h->mgraph) {
-        cudaGraphExecDestroy(h->mgraph);
-        h->mgraph = nullptr;
-        h->mgraph_R = 0;
+    if (h->mos_host) {
+        cudaStreamSynchronize(h->work);
+        cudaFreeHost(h->mos_host);
+        h->mos_host = nullptr;
     }
+    if (cudaMallocHost(&h->mos_host, sizeof(double) * 8 * R) != cudaSuccess) return UAAMG_ERR_OOM;
     h->multi_R = R;
     return UAAMG_OK;
 }

@@ -105,3 +105,40 @@ def test_cancel_withdraws_queued_requests_only():
             assert r[0] == 0
             assert np.linalg.norm(np.ones(A.n) - Asp @ r[1]) <= tol * np.sqrt(A.n) * 1.0001
     assert stats["done"] == 1 + len(small) // 2 + len(small) % 2
+
+
+def test_requests_for_different_matrices_share_one_batch():
+    """With the one worker busy, requests for three different matrices (two of them twice)
+    queue up; the next batch takes all six at once, as three systems of one
+    uaamg_solve_batch call, and every answer meets the bars of solving it alone."""
+    tol = 1e-8
+    blocker = I.grid3d(48, sigma=0.25, seed=9)
+    mats = [I.grid2d(50, 41), I.rgg(6000, 8.0, seed=31), I.grid3d(14, sigma=0.25, seed=32)]
+    params = U.uaamg_default_params(max_agg_size=0, kcycle_ratio=3.0)
+    rng = np.random.default_rng(5)
+    reqs = [(m, rng.uniform(-1, 1, mats[m].n)) for m in (0, 1, 2, 0, 1, 2)]
+    srv = U.Server(params, workers=1, max_batch=16)
+    try:
+        t0 = srv.submit(blocker.rowptr, blocker.col, blocker.val, np.ones(blocker.n), tol)
+        ts = [srv.submit(mats[m].rowptr, mats[m].col, mats[m].val, b, tol) for m, b in reqs]
+        assert srv.wait(t0)[0] == 0
+        answers = [srv.wait(t) for t in ts]
+    finally:
+        srv.close()
+    assert all(a[5] == len(reqs) for a in answers), [a[5] for a in answers]
+    handles = [U.uaamg_setup(A.rowptr, A.col, A.val, params) for A in mats]
+    try:
+        for (m, b), (st, x, it, rr, lat, batch) in zip(reqs, answers):
+            A = mats[m]
+            Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+            bn = np.linalg.norm(b)
+            assert st == 0
+            assert np.linalg.norm(b - Asp @ x) <= tol * bn * 1.0001
+            xa = np.zeros(A.n)
+            st1, it1, _ = U.uaamg_solve(handles[m], b, xa, tol)
+            assert st1 == 0
+            assert np.linalg.norm(Asp @ (x - xa)) <= 2.0001 * tol * bn
+            assert abs(it - it1) <= 3
+    finally:
+        for h in handles:
+            U.uaamg_free(h)
