@@ -179,6 +179,9 @@ def bench_params(U, precision, profile_class=0):
                                   use_graphs=0 if EAGER else 1, **BENCH_PARAMS, **extra)
 
 
+_LAST_X = {}  # the headline solve's solution, compared with the oracle's on rank 0
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -211,6 +214,7 @@ def run_gpu(args, rank, world):
                 raise RuntimeError(f"solve status {st} after {it} iterations, relres {rr}")
             s = U.uaamg_get_stats(h)
             s["levels"] = U.uaamg_num_levels(h)
+            s["coarsest_n"] = U.uaamg_level_info(h, s["levels"] - 1)[0]
             prof = U.uaamg_get_profile(h) if profile_class else None
             return it, rr, s, prof
         finally:
@@ -301,6 +305,7 @@ def run_gpu(args, rank, world):
     Asp = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
     xh = xd.cpu().numpy()
     relres_host = float(np.linalg.norm(b - Asp @ xh) / np.linalg.norm(b))
+    _LAST_X["headline"] = xh
 
     t_max = job_time(total_ms / 1000.0, world, dev)
     value = args.steps * world / t_max
@@ -368,7 +373,8 @@ def run_gpu(args, rank, world):
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                        "p99": round(float(np.percentile(lat, 99)), 3)},
         "iterations": int(np.median(its)), "relres_host_fp64": relres_host,
-        "levels": stats["levels"], "opc": round(stats["opc"], 3),
+        "levels": stats["levels"], "coarsest_n": stats["coarsest_n"],
+        "opc": round(stats["opc"], 3),
         "grid_complexity": round(stats["grid_complexity"], 3),
         "plain_fp64": None if not p_rec else {
             "value": round(len(p_lat) / (p_total / 1000.0), 3), "unit": "solves/s",
@@ -535,6 +541,54 @@ def run_c4(warmup=1, steps=1):
             "generate_s": round(t_gen, 2), "batched_mixed": batched, "plain_fp64": plain}
 
 
+def run_poisson64(steps=20, warmup=5):
+    """The 2D 5-point Poisson problem on the 64 x 64 grid (n = 4096; the paper's default
+    parameters, coarsest level at most 64 unknowns): L2-resident and launch-bound, so its
+    metric is the latency of one setup + solve, in mixed precision and in FP64."""
+    import torch
+
+    from paper_1302_2547_gb300 import _lib as U
+    from paper_1302_2547_gb300 import inputs as I
+
+    A = I.poisson2d_64()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        rp, cc, vv = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+        b = torch.from_numpy(I.rhs_uniform(A.n, I.RHS_SEED)).to(dev)
+        x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    stream.synchronize()
+    out = {"workload": f"poisson2d 64x64 interior, Dirichlet, unit weights (n={A.n}, "
+                       f"nnz={A.nnz})", "params": "defaults (t = 5, coarse_size 64)"}
+    for name, prec in (("mixed", U.UAAMG_MIXED), ("fp64", U.UAAMG_FP64)):
+        p = U.uaamg_default_params(precision=prec)
+        lat, slv, its = [], [], []
+        for k in range(warmup + steps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            h = U.uaamg_setup(rp, cc, vv, p, stream=stream)
+            e[1].record(stream)
+            st, it, rr = U.uaamg_solve(h, b, x, TOL)
+            e[2].record(stream)
+            stream.synchronize()
+            nlev = U.uaamg_num_levels(h)
+            nco = U.uaamg_level_info(h, nlev - 1)[0]
+            U.uaamg_free(h)
+            if st != 0:
+                raise RuntimeError(f"poisson64 solve status {st}")
+            if k >= warmup:
+                lat.append(e[0].elapsed_time(e[2]))
+                slv.append(e[1].elapsed_time(e[2]))
+                its.append(it)
+        out[name] = {"latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                                    "p99": round(float(np.percentile(lat, 99)), 3)},
+                     "solve_ms": {"p50": round(float(np.percentile(slv, 50)), 3),
+                                  "p99": round(float(np.percentile(slv, 99)), 3)},
+                     "solves_per_s": round(1000.0 / float(np.mean(lat)), 1),
+                     "iterations": int(np.median(its)), "levels": nlev, "coarsest_n": nco}
+    return out
+
+
 def run_rgg(steps=3, warmup=1):
     """Setup + mixed solve of the 4M-point random geometric graph (inputs resident), timed
     like the main line; reported beside it, not as the headline."""
@@ -632,83 +686,142 @@ def run_sra(rounds=2, steps=3, warmup=1):
                              "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"}}}
 
 
-def run_serving(n_requests=120, seed=2024):
-    """The solve service (uaamg_server_*) under a Poisson stream of requests, shaped like the
-    serving workload with smaller sizes so that it runs in seconds: 12 matrices (2D grid, 3D
-    grid with lognormal weights, random geometric graph of mean degree 8), sizes
-    log-uniform in [1e4, 1e6]; 30% of the requests repeat an already seen matrix (cached
-    hierarchy, new right-hand side), the rest bring a matrix the cache has not seen (new
-    key: a setup).  The arrival rate is 70% of the capacity measured one request at a time.
-    Latency = the server's time from submit to result."""
+SERVING = dict(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
+               budget_bytes=150 << 30, workers=4, max_batch=16, load=0.7,
+               sweep=((0.5, 300), (0.9, 300)))
+
+
+def run_serving(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
+                budget_bytes=150 << 30, workers=4, max_batch=16, load=0.7, sweep=(),
+                seed=2024):
+    """The solve service (uaamg_server_*) under a Poisson stream of requests: sizes
+    log-uniform in [nmin, nmax], kinds 2D grid / 3D grid with lognormal weights / random
+    geometric graph of mean degree 8 in equal parts; 30% of the requests repeat a matrix the
+    stream brought before (cached hierarchy, new right-hand side), the rest bring a matrix
+    the cache has not seen.  A request's matrix is the base graph of its kind nearest to its
+    size (per_kind bases spaced evenly in log) with every weight scaled by a random factor
+    in [0.5, 2]: a distinct matrix for the cache with the work of a new one of that size.
+    The arrival rate is `load` times the capacity measured one new request at a time; the
+    first `warmup` requests are not counted.  Latency = the server's time from submit to
+    result.  `sweep` repeats the stream at other loads with fewer requests."""
     from paper_1302_2547_gb300 import _lib as U
     from paper_1302_2547_gb300 import inputs as I
 
+    t_gen = time.perf_counter()
+    bases = I.serving_bases(per_kind, nmin, nmax, processes=min(16, os.cpu_count() or 1))
+    t_gen = time.perf_counter() - t_gen
+    logs = {k: np.log([b[1] for b in bases if b[0] == k]) for k in range(3)}
+    by_kind = {k: [b[2] for b in bases if b[0] == k] for k in range(3)}
+    # one service per kind, each with that kind's method parameters and a third of the budget
+    params = [U.uaamg_default_params(**C4_GRID2D_PARAMS), U.uaamg_default_params(**BENCH_PARAMS),
+              U.uaamg_default_params(**RGG_PARAMS)]
     rng = np.random.default_rng(seed)
-    pool = []
-    for k in range(12):
-        n = int(np.exp(rng.uniform(np.log(1e4), np.log(1e6))))
-        if k % 3 == 0:
-            A = I.grid2d(max(8, int(round(np.sqrt(n)))))
-        elif k % 3 == 1:
-            A = I.grid3d(max(4, int(round(n ** (1.0 / 3.0)))), sigma=0.25, seed=3000 + k)
-        else:
-            A = I.rgg(n, 8.0, seed=3000 + k)
-        pool.append(A)
-    srv = U.Server(U.uaamg_default_params(**BENCH_PARAMS), budget_bytes=150 << 30, workers=4,
-                   max_batch=16)
     next_key = [1]
 
-    def submit(m, key=None):
-        A = pool[m]
-        if key is None:
-            key = next_key[0]
-            next_key[0] += 1
-        b = rng.uniform(-1.0, 1.0, A.n)
-        return srv.submit(A.rowptr, A.col, A.val, b, TOL, key=key), key
+    def draw():  # (kind, base index, scale) of a request bringing a new matrix
+        k = int(rng.integers(0, 3))
+        n = np.exp(rng.uniform(np.log(nmin), np.log(nmax)))
+        i = int(np.argmin(np.abs(logs[k] - np.log(n))))
+        return k, i, float(np.exp(rng.uniform(np.log(0.5), np.log(2.0))))
 
-    try:
-        # capacity: requests with new matrices, one at a time
-        t0 = time.perf_counter()
-        for m in range(len(pool)):
-            t, _ = submit(m)
-            st, _, _, rr, _, _ = srv.wait(t)
-            if st != 0:
-                raise RuntimeError(f"serving warm-up status {st}")
-        service = (time.perf_counter() - t0) / len(pool)
-        lam = 0.7 / service
-        arrivals = np.cumsum(rng.exponential(1.0 / lam, n_requests))
-        seen = []  # (matrix, key) pairs whose hierarchy the server holds
-        tickets = []
+    def stream(servers, count, lam, label):
+        import queue as Q
+        import threading
+
+        seen = []  # (kind, base, scale, key) of matrices the stream brought
         new = 0
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, count))
+        pending = Q.Queue()
+        res = []
+
+        def waiter():  # collects answers as they come, so finished requests free their copies
+            while True:
+                item = pending.get()
+                if item is None:
+                    return
+                res.append(item[0].wait(item[1]))
+
+        th = threading.Thread(target=waiter, daemon=True)
+        th.start()
         t0 = time.perf_counter()
         for a in arrivals:
+            if seen and rng.uniform() < 0.3:
+                k, i, c, key = seen[int(rng.integers(0, len(seen)))]
+            else:
+                k, i, c = draw()
+                key = next_key[0]
+                next_key[0] += 1
+                seen.append((k, i, c, key))
+                new += 1
+            A = by_kind[k][i]
+            val = A.val * c
+            b = rng.uniform(-1.0, 1.0, A.n)
             d = t0 + a - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-            if seen and rng.uniform() < 0.3:
-                m, key = seen[int(rng.integers(0, len(seen)))]
-                t, _ = submit(m, key)
-            else:
-                m = int(rng.integers(0, len(pool)))
-                t, key = submit(m)
-                seen.append((m, key))
-                new += 1
-            tickets.append(t)
-        res = [srv.wait(t) for t in tickets]
+            srv = servers[k]
+            pending.put((srv, srv.submit(A.rowptr, A.col, val, b, TOL, key=key)))
+        pending.put(None)
+        th.join()
         wall = time.perf_counter() - t0
-        stats = srv.stats()
+        return res, wall, new
+
+    servers = [U.Server(params[k], budget_bytes=budget_bytes // 3, workers=workers,
+                        max_batch=max_batch) for k in range(3)]
+    out = {"workload": f"Poisson arrivals, sizes log-uniform {nmin:.0e}-{nmax:.0e} "
+                       f"(2D grid, 3D grid lognormal, RGG mean degree 8), 30% repeat a "
+                       f"cached matrix, tol {TOL}",
+           "requests": n_requests, "warmup": warmup, "budget_bytes": budget_bytes,
+           "workers_per_server": workers, "max_batch": max_batch,
+           "servers": "one service per kind (its own parameters), a third of the budget each",
+           "bases_per_kind": per_kind, "generate_s": round(t_gen, 1)}
+    try:
+        # capacity: requests with new matrices, one at a time
+        cap_n = 24
+        t0 = time.perf_counter()
+        for _ in range(cap_n):
+            k, i, c = draw()
+            A = by_kind[k][i]
+            srv = servers[k]
+            key = next_key[0]
+            next_key[0] += 1
+            t = srv.submit(A.rowptr, A.col, A.val * c, rng.uniform(-1, 1, A.n), TOL, key=key)
+            st, _, _, rr, _, _ = srv.wait(t)
+            if st != 0:
+                raise RuntimeError(f"serving capacity request status {st}")
+        service = (time.perf_counter() - t0) / cap_n
+        out["capacity_per_s_one_at_a_time"] = round(1.0 / service, 2)
+        lam = load / service
+        if warmup:
+            stream(servers, warmup, lam, "warmup")
+        res, wall, new = stream(servers, n_requests, lam, "main")
+        lat = np.array([r[4] for r in res])
+        failed = sum(1 for r in res if r[0] != 0 or not (r[3] <= TOL))
+        sts = [sv.stats() for sv in servers]
+        out.update({"lambda_per_s": round(lam, 2), "offered_load": load,
+                    "new_matrix_fraction": round(new / n_requests, 3),
+                    "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                    "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                    "solves_per_s": round(n_requests / wall, 2), "failed": failed,
+                    "batch_mean": round(float(np.mean([r[5] for r in res])), 2),
+                    "batches": sum(x["batches"] for x in sts),
+                    "cache_hits": sum(x["cache_hits"] for x in sts),
+                    "setups": sum(x["setups"] for x in sts),
+                    "rejected": sum(x["rejected"] for x in sts)})
+        out["sweep"] = []
+        for ld, cnt in sweep:
+            r2, w2, _ = stream(servers, cnt, ld / service, f"sweep {ld}")
+            l2 = np.array([r[4] for r in r2])
+            out["sweep"].append({"offered_load": ld, "requests": cnt,
+                                 "lambda_per_s": round(ld / service, 2),
+                                 "p50_ms": round(float(np.percentile(l2, 50)), 2),
+                                 "p99_ms": round(float(np.percentile(l2, 99)), 2),
+                                 "solves_per_s": round(cnt / w2, 2),
+                                 "failed": sum(1 for r in r2 if r[0] != 0 or not (r[3] <= TOL))})
     finally:
-        srv.close()
-    lat = np.array([r[4] for r in res])
-    failed = sum(1 for r in res if r[0] != 0 or not (r[3] <= TOL))
-    return {"requests": n_requests, "lambda_per_s": round(lam, 2), "offered_load": 0.7,
-            "new_matrix_fraction": round(new / n_requests, 3),
-            "p50_ms": round(float(np.percentile(lat, 50)), 2),
-            "p99_ms": round(float(np.percentile(lat, 99)), 2),
-            "solves_per_s": round(n_requests / wall, 2), "failed": failed,
-            "batches": stats["batches"], "cache_hits": stats["cache_hits"],
-            "setups": stats["setups"], "workers": 4, "max_batch": 16,
-            "sizes": "log-uniform 1e4-1e6; 2D grid, 3D grid, RGG (mean degree 8)"}
+        for s in servers:
+            s.close()
+    return out
 
 
 def run_cpu_baseline(sample_steps=1):
@@ -729,11 +842,29 @@ def run_cpu_baseline(sample_steps=1):
         tv.append(t2 - t1)
         assert st == 0
         del H
+    _LAST_X["oracle"] = (x, A)
     return {"value": round(len(t) / sum(t), 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(t)} full setup+solve of the 128^3 system (serial C, FP64), "
                       f"{sum(t):.1f} s",
             "setup_ms": round(1000 * float(np.median(ts)), 1),
             "solve_ms": round(1000 * float(np.median(tv)), 1), "iterations": int(it)}, t, it
+
+
+def err_vs_oracle():
+    """The headline solution against the oracle's for the same system and right-hand side:
+    both stop at |b - A x| <= 1e-8 |b|, so they differ by up to about kappa(A) 1e-8 in the
+    2-norm and 1e-8 |b| |A^{-1/2}| in the A-norm."""
+    import scipy.sparse as sp
+
+    if "headline" not in _LAST_X or "oracle" not in _LAST_X:
+        return None
+    x, (xo, A) = _LAST_X["headline"], _LAST_X["oracle"]
+    Asp = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+    d = x - xo
+    return {"A_norm_rel": float(np.sqrt(d @ (Asp @ d)) / np.sqrt(xo @ (Asp @ xo))),
+            "two_norm_rel": float(np.linalg.norm(d) / np.linalg.norm(xo)),
+            "max_abs_rel": float(np.max(np.abs(d)) / np.max(np.abs(xo))),
+            "of": "the mixed-precision headline solve vs the FP64 oracle's, same b, tol 1e-8"}
 
 
 def _mem_available() -> int:
@@ -840,8 +971,10 @@ def main():
                     help="print only the batched workload's measurement as one JSON line")
     ap.add_argument("--c4-systems", type=int, default=0,
                     help="run only the first k systems of the batched workload")
-    ap.add_argument("--rgg", action="store_true",
-                    help="also time the 4M-point random geometric graph (about a minute)")
+    ap.add_argument("--skip-rgg", action="store_true",
+                    help="do not time the 4M-point random geometric graph")
+    ap.add_argument("--skip-poisson64", action="store_true",
+                    help="do not time the 64 x 64 Poisson problem's latency")
     ap.add_argument("--tma-rows", type=int, default=None,
                     help="row threshold of the TMA-staged row-block kernels (0 = off)")
     ap.add_argument("--fuse-below", type=int, default=None,
@@ -913,15 +1046,24 @@ def main():
                 out["c4_batched"] = run_c4()
             except Exception as e:  # reported, not hidden: the main line still stands
                 out["c4_batched"] = {"error": f"{type(e).__name__}: {e}"}
-        if world == 1 and args.rgg:
-            out["rgg_4m"] = run_rgg()
+        if world == 1 and not args.skip_rgg:
+            try:
+                out["rgg_4m"] = run_rgg()
+            except Exception as e:  # reported, not hidden: the main line still stands
+                out["rgg_4m"] = {"error": f"{type(e).__name__}: {e}"}
+        if world == 1 and not args.skip_poisson64:
+            try:
+                out["poisson2d_64"] = run_poisson64()
+            except Exception as e:  # reported, not hidden: the main line still stands
+                out["poisson2d_64"] = {"error": f"{type(e).__name__}: {e}"}
         if world == 1 and not args.skip_serving:
             try:
-                out["serving"] = run_serving()
+                out["serving"] = run_serving(**SERVING)
             except Exception as e:  # reported, not hidden: the main line still stands
                 out["serving"] = {"error": f"{type(e).__name__}: {e}"}
         if world == 1 and not args.skip_cpu_baseline:
             out["cpu_baseline"] = run_cpu_baseline(1)[0]
+            out["err_vs_oracle"] = err_vs_oracle()
             try:
                 out["cpu_baseline_allcores"] = run_cpu_baseline_allcores()
             except Exception as e:  # reported, not hidden: the main line still stands

@@ -277,8 +277,10 @@ const char* uaamg_status_string(int status);
  * submit) are queued; `workers` host threads, each with its own CUDA stream, take them in
  * arrival order.  Hierarchies stay cached on the device, keyed by matrix_key (or, when it
  * is 0, a 64-bit FNV-1a hash of n and the three CSR arrays); least recently used idle ones
- * are freed to admit new ones within budget_bytes (0 = no budget; the budget is applied
- * library-wide with uaamg_set_memory_budget while the server lives).  A request whose
+ * are freed to admit new ones within budget_bytes (0 = no budget), counted per service by
+ * each hierarchy's admission estimate (the CSR, its coarse levels, setup scratch and the
+ * solve workspace of up to max_batch columns).  While services with a budget live, the
+ * library-wide cap of uaamg_set_memory_budget is the sum of their budgets.  A request whose
  * estimated hierarchy cannot fit the budget is answered with UAAMG_ERR_BUDGET; one that
  * fits after eviction waits until memory frees.  Continuous batching: a free worker takes,
  * in arrival order, every queued request whose matrix no other worker is using and whose

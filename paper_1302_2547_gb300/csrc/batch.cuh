@@ -5,7 +5,7 @@
 // of R columns, interleaved [n][R] as for uaamg_solve_many.  A launch covers every
 // participating system at one node of the K-cycle (Section 4.3): its blocks are tiles of
 // the systems' rows, listed per launch as segments (one per system, in system order), and
-// each block finds its system by a binary search over the segments' first tiles.  Inner
+// each block reads its system and tile from the launch's per-block table.  Inner
 // products are reduced per system and per column in a fixed order (a tree inside a tile,
 // then the system's tiles in order by the last of its tiles to finish), and a system's
 // tiles depend only on its own level size and column count, so a system's result is the
@@ -51,8 +51,9 @@ struct BLevel {
 // Arguments of every batched kernel.
 struct BArgs {
     const BLevel* lev;  // [nsys][kMaxLevels]
-    const int* sys;     // [nseg] systems of the launch, ascending
-    const int* tile0;   // [nseg + 1] first tile of each segment
+    // per block of the launch: its system, its tile within the system, the system's tile
+    // count and the launch's first tile of that system (where its partial sums start)
+    const int4* tinfo;
     int nseg;
     const int* active;  // [nsys] 0 once every column of the system has converged
     int level;
@@ -83,8 +84,8 @@ __host__ __device__ inline int b_tiles(int n, int R) {
     return n > 0 ? (n + t - 1) / t : 0;
 }
 
-// Launchers (kern_batch.cu).  `tiles` is the grid (tile0[nseg]); every launcher returns a
-// status.
+// Launchers (kern_batch.cu).  `tiles` is the launch's block count (one block per tile);
+// every launcher returns a status.
 enum BKind {
     BK_ROW = 0,   // SpMV-based row kernel (mode, ndots as the single-system RB_* modes)
     BK_RESTRICT,  // r_c = P^T s

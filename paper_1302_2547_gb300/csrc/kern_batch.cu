@@ -14,26 +14,19 @@ namespace uaamg {
 
 constexpr int kBGather = 8;  // row entries whose loads a thread issues together
 
-// The tile of this block: its system (binary search over the segments' first tiles), the
-// tile's index within the system and the system's tile count at this launch.
+// The tile of this block (one 16-byte load of the launch's table): its system, the tile's
+// index within the system and the system's tile count at this launch.
 struct BTile {
-    int seg, sys, tile, ntiles;
+    int sys, tile, ntiles, part0;
     const BLevel* L;
 };
 
 __device__ __forceinline__ bool b_enter(const BArgs& a, BTile& t) {
-    const int b = blockIdx.x;
-    int lo = 0, hi = a.nseg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(a.tile0 + mid) <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    t.seg = lo;
-    t.sys = __ldg(a.sys + lo);
-    const int f = __ldg(a.tile0 + lo);
-    t.tile = b - f;
-    t.ntiles = __ldg(a.tile0 + lo + 1) - f;
+    const int4 ti = __ldg(a.tinfo + blockIdx.x);
+    t.sys = ti.x;
+    t.tile = ti.y;
+    t.ntiles = ti.z;
+    t.part0 = ti.w;
     t.L = a.lev + (size_t)t.sys * kMaxLevels + a.level;
     return a.active[t.sys] != 0;
 }
@@ -94,7 +87,7 @@ __device__ __forceinline__ bool b_reduce(const double (&v)[ND], int lg, int R, c
 
 template <int ND>
 __device__ __forceinline__ double* b_part(const BArgs& a, const BTile& t) {
-    return a.partials + (size_t)__ldg(a.tile0 + t.seg) * ND * kBPartStride;
+    return a.partials + (size_t)t.part0 * ND * kBPartStride;
 }
 __device__ __forceinline__ double* b_os(const BArgs& a, const BTile& t) {
     return a.lev[(size_t)t.sys * kMaxLevels].os;

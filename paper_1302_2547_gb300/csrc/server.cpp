@@ -65,6 +65,23 @@ uint64_t fnv1a(const void* p, size_t bytes, uint64_t h) {
     return h;
 }
 
+// The library-wide device-memory cap while services live: the sum of their budgets.
+std::mutex g_budget_mu;
+uint64_t g_budget_sum = 0;
+int g_budget_servers = 0;
+
+void add_budget(uint64_t b, int sign) {
+    std::lock_guard<std::mutex> lk(g_budget_mu);
+    if (sign > 0) {
+        g_budget_sum += b;
+        g_budget_servers++;
+    } else {
+        g_budget_sum -= b;
+        g_budget_servers--;
+    }
+    uaamg_set_memory_budget(g_budget_servers > 0 ? g_budget_sum : 0);
+}
+
 }  // namespace
 
 struct uaamg_server {
@@ -92,10 +109,16 @@ struct uaamg_server {
             }
         return nullptr;
     }
+    // Device bytes this service's cached hierarchies may hold (their admission estimates).
+    uint64_t held() const {
+        uint64_t b = 0;
+        for (auto& e : cache) b += e.bytes;
+        return b;
+    }
     // Evicts least recently used idle hierarchies until `need` more bytes fit the budget.
     bool make_room(uint64_t need) {
         if (!budget) return true;
-        while (uaamg_memory_in_use() + need > budget) {
+        while (held() + need > budget) {
             auto victim = cache.end();
             for (auto it = cache.begin(); it != cache.end(); ++it)
                 if (it->users == 0) victim = it;
@@ -301,6 +324,8 @@ void uaamg_server::worker_main(int wid) {
                 q->latency_ms =
                     std::chrono::duration<double, std::milli>(t_end - q->t_submit).count();
                 q->done = true;
+                q->A.reset();  // the host copies of an answered request are no longer needed
+                std::vector<double>().swap(q->b);
             }
         }
         n_done += taken;
@@ -327,7 +352,7 @@ int uaamg_server_create(const uaamg_params* p, uint64_t budget_bytes, int32_t wo
         delete s;
         return UAAMG_ERR_CUDA;
     }
-    if (budget_bytes) uaamg_set_memory_budget(budget_bytes);
+    if (budget_bytes) add_budget(budget_bytes, +1);
     for (int w = 0; w < workers; w++) s->workers.emplace_back(&uaamg_server::worker_main, s, w);
     *out = s;
     return UAAMG_OK;
@@ -444,7 +469,7 @@ void uaamg_server_destroy(uaamg_server* s) {
         if (e.h) uaamg_free(e.h);
     }
     s->cache.clear();
-    if (s->budget) uaamg_set_memory_budget(0);
+    if (s->budget) add_budget(s->budget, -1);
     delete s;
 }
 

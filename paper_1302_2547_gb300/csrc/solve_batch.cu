@@ -29,7 +29,7 @@ struct Rec {
     int s_r, s_x, s_y, s_y2, s_d1, s_d2, s_e;
     int res_os, res_row, outer;
     bool dbl;    // FP64 kernel whatever the cycle's precision
-    int off;     // offset of the launch's table in the table buffer (ints)
+    long long off;  // offset of the launch's per-block table in the table buffer (int4s)
     int nseg, tiles;
 };
 
@@ -45,7 +45,7 @@ Rec rec(int kind, int level) {
 struct Plan {
     const std::vector<BLevel>* lev = nullptr;  // [nsys][kMaxLevels]
     std::vector<int> nlev;
-    std::vector<int> tab;  // per launch: sys[nseg], tile0[nseg + 1]
+    std::vector<int4> tab;  // per launch, per block: system, tile, tiles, first tile
     std::vector<Rec> recs;
     long long max_part = 0;  // doubles of partial sums the widest launch needs
 
@@ -58,16 +58,15 @@ struct Plan {
         return b_tiles(B.n, B.R);
     }
 
-    // Appends the launch's table and returns the record with its offset and grid.
-    Rec table(Rec r, const std::vector<int>& parts, std::vector<int>* out) const {
-        r.off = (int)out->size();
+    // Appends the launch's per-block table and returns the record with its offset and grid.
+    Rec table(Rec r, const std::vector<int>& parts, std::vector<int4>* out) const {
+        r.off = (long long)out->size();
         r.nseg = (int)parts.size();
-        for (int s : parts) out->push_back(s);
         int acc = 0;
-        out->push_back(0);
         for (int s : parts) {
-            acc += tiles_of(r, s);
-            out->push_back(acc);
+            const int nt = tiles_of(r, s);
+            for (int t = 0; t < nt; t++) out->push_back(make_int4(s, t, nt, acc));
+            acc += nt;
         }
         r.tiles = acc;
         return r;
@@ -205,8 +204,8 @@ struct Batch {
     bool mixed = false;
     int nsys = 0;
     BLevel* d_lev = nullptr;
-    int* d_tab = nullptr;
-    int* d_chk = nullptr;  // tables of the convergence checks
+    int4* d_tab = nullptr;
+    int4* d_chk = nullptr;  // tables of the convergence checks
     int* d_active = nullptr;
     double* d_os = nullptr;
     double* h_os = nullptr;  // pinned mirror
@@ -216,11 +215,10 @@ struct Batch {
     long long graph_nodes = 0;
 };
 
-int run(Batch& bt, const Rec& r, const int* tab) {
+int run(Batch& bt, const Rec& r, const int4* tab) {
     BArgs a{};
     a.lev = bt.d_lev;
-    a.sys = tab + r.off;
-    a.tile0 = tab + r.off + r.nseg;
+    a.tinfo = tab + r.off;
     a.nseg = r.nseg;
     a.active = bt.d_active;
     a.level = r.level;
@@ -349,8 +347,8 @@ int solve_batch(Handle* const* hs, int nsys, const int* R, const double* const* 
 
     // device buffers of the batch (stream-ordered, released at the end)
     bt.d_lev = dalloc<BLevel>(&bt.bh, lev.size(), &st);
-    bt.d_tab = dalloc<int>(&bt.bh, plan.tab.size(), &st);
-    bt.d_chk = dalloc<int>(&bt.bh, 2 * (size_t)nsys + 1, &st);
+    bt.d_tab = dalloc<int4>(&bt.bh, plan.tab.size(), &st);
+    bt.d_chk = dalloc<int4>(&bt.bh, (size_t)r_resid.tiles, &st);
     bt.d_active = dalloc<int>(&bt.bh, nsys, &st);
     bt.d_os = dalloc<double>(&bt.bh, (size_t)os_off[nsys], &st);
     bt.partials = dalloc<double>(&bt.bh, (size_t)plan.max_part, &st);
@@ -358,7 +356,7 @@ int solve_batch(Handle* const* hs, int nsys, const int* R, const double* const* 
     if (st == UAAMG_OK && cudaMallocHost(&bt.h_os, sizeof(double) * os_off[nsys]) != cudaSuccess)
         st = UAAMG_ERR_OOM;
     std::vector<int> h_active(nsys, 1);
-    std::vector<int> h_chk;
+    std::vector<int4> h_chk;
     int status = UAAMG_OK;
     std::vector<std::vector<int>> colact(nsys);
     std::vector<double> bn((size_t)os_off[nsys] / 8), rn((size_t)os_off[nsys] / 8);
@@ -384,7 +382,7 @@ int solve_batch(Handle* const* hs, int nsys, const int* R, const double* const* 
         for (int k = 0; k < 8 * R[s]; k++) o[k] = (k >= 6 * R[s]) ? 1.0 : 0.0;
     }
     cudaMemcpyAsync(bt.d_lev, lev.data(), sizeof(BLevel) * lev.size(), cudaMemcpyHostToDevice, ws);
-    cudaMemcpyAsync(bt.d_tab, plan.tab.data(), sizeof(int) * plan.tab.size(),
+    cudaMemcpyAsync(bt.d_tab, plan.tab.data(), sizeof(int4) * plan.tab.size(),
                     cudaMemcpyHostToDevice, ws);
     cudaMemcpyAsync(bt.d_active, h_active.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, ws);
     cudaMemcpyAsync(bt.d_os, bt.h_os, sizeof(double) * os_off[nsys], cudaMemcpyHostToDevice, ws);
@@ -483,7 +481,7 @@ int solve_batch(Handle* const* hs, int nsys, const int* R, const double* const* 
         if (!check.empty()) {  // confirm with the recomputed FP64 residual of those systems
             h_chk.clear();
             Rec rc = plan.table(resid_rec(), check, &h_chk);
-            cudaMemcpyAsync(bt.d_chk, h_chk.data(), sizeof(int) * h_chk.size(),
+            cudaMemcpyAsync(bt.d_chk, h_chk.data(), sizeof(int4) * h_chk.size(),
                             cudaMemcpyHostToDevice, ws);
             st = run(bt, rc, bt.d_chk);
             if (st == UAAMG_OK) st = read_os();

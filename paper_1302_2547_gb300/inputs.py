@@ -254,3 +254,31 @@ def batch_mix(nsys: int = 512, nmin: int = 1024, nmax: int = 262144,
         with mp.get_context("spawn").Pool(processes) as pool:
             return pool.map(_batch_member, jobs, chunksize=4)
     return [_batch_member(j) for j in jobs]
+
+
+def _serving_base(args):
+    kind, n, seed = args
+    if kind == 0:
+        side = max(8, int(round(math.sqrt(n))))
+        return grid2d(side, side, name=f"serve_grid2d_{side}")
+    if kind == 1:
+        side = max(4, int(round(n ** (1.0 / 3.0))))
+        return grid3d(side, sigma=0.25, seed=seed, name=f"serve_grid3d_{side}")
+    return rgg(int(n), 8.0, seed=seed, name=f"serve_rgg_{int(n)}")
+
+
+def serving_bases(per_kind: int = 8, nmin: float = 1e4, nmax: float = 8e6,
+                  seed: int = MATRIX_SEED + 5, processes: int = 0) -> list:
+    """Base graphs of the serving stream: for each kind (2D grid, 3D grid with lognormal
+    weights, random geometric graph of mean degree 8), `per_kind` sizes spaced evenly in
+    log between nmin and nmax.  Returns [(kind, size, CSR)], sizes ascending per kind."""
+    sizes = np.exp(np.linspace(math.log(nmin), math.log(nmax), per_kind))
+    jobs = [(k, float(n), seed + 10 * k + i) for k in range(3) for i, n in enumerate(sizes)]
+    if processes > 1:
+        import multiprocessing as mp
+
+        with mp.get_context("spawn").Pool(processes) as pool:
+            mats = pool.map(_serving_base, jobs, chunksize=1)
+    else:
+        mats = [_serving_base(j) for j in jobs]
+    return [(j[0], j[1], m) for j, m in zip(jobs, mats)]
