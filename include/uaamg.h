@@ -262,6 +262,12 @@ int uaamg_set_profiling(uaamg_handle* h, int32_t kclass);
 int uaamg_get_profile(const uaamg_handle* h, int64_t* launches, double* total_ms,
                       double* bytes_per_launch);
 
+/* The device's FP64 fused multiply-add rate (FMA per second, an FMA being two floating-point
+ * operations), measured with CUDA events over `chains` (1 or 8) independent FMA recurrences
+ * per thread on a grid of resident blocks on every SM (1: latency-bound, 8: the pipe's
+ * throughput).  The denominator of the FP64 roofline; runs on the legacy default stream. */
+int uaamg_measure_fp64_fma(int32_t chains, double* fma_per_s);
+
 /* Total kernels launched by this library in this process (all handles). */
 int64_t uaamg_total_launches(void);
 /* Library-wide cap on device bytes held by all handles (0 = no cap), and the bytes held. */

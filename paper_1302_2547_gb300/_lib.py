@@ -31,7 +31,7 @@ EXPORTS = [
     "uaamg_status_string", "uaamg_aggregate_static", "uaamg_solve_many",
     "uaamg_server_create", "uaamg_server_submit", "uaamg_server_poll", "uaamg_server_wait",
     "uaamg_server_stats", "uaamg_server_destroy", "uaamg_server_cancel",
-    "uaamg_solve_batch", "uaamg_setup_batch",
+    "uaamg_solve_batch", "uaamg_setup_batch", "uaamg_measure_fp64_fma",
 ]
 
 
@@ -116,6 +116,7 @@ def lib() -> C.CDLL:
             "uaamg_server_cancel": (C.c_int, [P, U64, C.POINTER(I32)]),
             "uaamg_solve_batch": (C.c_int, [P, I32, P, P, P, D, P, P, P]),
             "uaamg_setup_batch": (C.c_int, [I32, P, P, I32, P, P]),
+            "uaamg_measure_fp64_fma": (C.c_int, [I32, C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -339,6 +340,13 @@ def uaamg_get_profile(h):
     n, ms, by = C.c_int64(), C.c_double(), C.c_double()
     check(lib().uaamg_get_profile(h, C.byref(n), C.byref(ms), C.byref(by)), "uaamg_get_profile")
     return n.value, ms.value, by.value
+
+
+def uaamg_measure_fp64_fma(chains: int = 8) -> float:
+    """FP64 FMA per second of the current device (1 or 8 independent chains per thread)."""
+    v = C.c_double(0.0)
+    check(lib().uaamg_measure_fp64_fma(chains, C.byref(v)), "uaamg_measure_fp64_fma")
+    return v.value
 
 
 def uaamg_total_launches() -> int:

@@ -51,6 +51,33 @@ struct Agg {
     int *agg = nullptr, *aggptr = nullptr, *members = nullptr;
 };
 
+// Algorithmic bytes of the profiled aggregation launch: every pass sweeps the adjacency of
+// its vertices twice (the maximum of the candidates' priorities within distance 1, then
+// the roots' test and their aggregates), and a sweep over V of the n vertices moves
+// V/n (4z + 4(n+1) + 8n + n) bytes: columns, row pointers, the priorities once (gathers
+// served by L2) and the state.  The first sweep of a pass covers every vertex (pull) or the
+// previous pass's candidates (push), as the kernel chooses; the second the pass's own
+// candidates (their counts are the kernel's per-pass slots).
+static int paa_profile_bytes(Handle* h, const Csr& G, const int* d_slots, int passes) {
+    std::vector<int> c(passes + 1, 0);
+    int st = check_cuda(cudaMemcpyAsync(c.data(), d_slots, sizeof(int) * (passes + 1),
+                                        cudaMemcpyDeviceToHost, h->work));
+    if (st == UAAMG_OK) st = check_cuda(cudaStreamSynchronize(h->work));
+    if (st) return st;
+    const double n = G.n, z = (double)G.nnz;
+    const double full = 4.0 * z + 4.0 * (n + 1.0) + 9.0 * n;
+    double bytes = 0.0;
+    int prev = G.n;
+    for (int p = 0; p <= passes; p++) {
+        const bool pull = p == 0 || (long long)prev * 4 > G.n;  // the kernel's kPullDiv rule
+        bytes += full * (pull ? 1.0 : (double)prev / n);
+        if (p < passes) bytes += full * (double)c[p] / n;
+        prev = c[p];
+    }
+    h->prof_bytes = bytes;
+    return UAAMG_OK;
+}
+
 // One aggregation stage on graph G: priorities with the given salt, the passes of
 // Algorithm 2, ascending coarse numbering.  Outputs are handle temporaries.
 static int aggregate_stage(Handle* h, int prof_level, const Csr& G, uint32_t salt, Scratch& S,
@@ -66,6 +93,9 @@ static int aggregate_stage(Handle* h, int prof_level, const Csr& G, uint32_t sal
     if ((st = read_back(h, S.d_tot, hb))) return st;
     out->passes = hb->ctrl.npasses;
     out->nc = hb->nc;
+    if (h->prof_class == UAAMG_KCLASS_PAA && prof_level == 0 &&
+        (st = paa_profile_bytes(h, G, S.pb.slots, out->passes)))
+        return st;
     if (out->nc >= G.n) return UAAMG_OK;  // no coarsening possible
     out->agg = dalloc<int>(h, G.n, &st, true);
     out->aggptr = dalloc<int>(h, out->nc + 1, &st, true);
@@ -92,6 +122,12 @@ static int assemble(Handle* h, int prof_level, const Csr& G, const Agg& a, Scrat
     cudaMemcpyAsync(C->rowptr + nc, S.d_tot + 2, sizeof(int), cudaMemcpyDeviceToDevice, h->work);
     if ((st = read_back(h, S.d_tot, hb))) return st;
     C->nnz = hb->nnzc;
+    if (h->prof_class == UAAMG_KCLASS_COARSE && prof_level == 0) {
+        // the assembly's minimum: the fine matrix and the aggregation once (agg, aggptr,
+        // members), the coarse matrix written once
+        const double n = G.n, z = (double)G.nnz, ncd = nc, zc = (double)C->nnz;
+        h->prof_bytes = z * 12.0 + 12.0 * n + zc * 12.0 + 4.0 * ncd;
+    }
     C->col = dalloc<int>(h, C->nnz, &st, true);
     C->val = dalloc<double>(h, C->nnz, &st, true);
     if (st) return st;

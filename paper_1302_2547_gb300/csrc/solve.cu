@@ -69,6 +69,8 @@ static double class_bytes(const Handle* h, int cls) {
     if (cls == UAAMG_KCLASS_SPMV64) return z * 12.0 + 4 * (n + 1) + 3 * n * 8.0;
     if (cls == UAAMG_KCLASS_SRA)  // FP64 operations the reshaping kernels counted
         return h->prof_launches > 0 ? h->prof_bytes / (double)h->prof_launches : 0.0;
+    if (cls == UAAMG_KCLASS_PAA || cls == UAAMG_KCLASS_COARSE)  // set by the setup
+        return h->prof_bytes;
     return 0.0;
 }
 
