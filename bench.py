@@ -745,7 +745,7 @@ def run_sra(rounds=2, steps=3, warmup=1):
 
 SERVING = dict(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
                budget_bytes=150 << 30, workers=4, max_batch=16, load=0.7,
-               sweep=((0.5, 300), (0.9, 300)))
+               sweep=((0.5, 200), (0.9, 200)))
 
 
 def run_serving(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
@@ -796,7 +796,9 @@ def run_serving(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
                 item = pending.get()
                 if item is None:
                     return
-                res.append(item[0].wait(item[1]))
+                _, ans = item[0].wait_answer(item[1])
+                ans["n"] = item[2]
+                res.append(ans)
 
         th = threading.Thread(target=waiter, daemon=True)
         th.start()
@@ -817,7 +819,7 @@ def run_serving(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
             if d > 0:
                 time.sleep(d)
             srv = servers[k]
-            pending.put((srv, srv.submit(A.rowptr, A.col, val, b, TOL, key=key)))
+            pending.put((srv, srv.submit(A.rowptr, A.col, val, b, TOL, key=key), A.n))
         pending.put(None)
         th.join()
         wall = time.perf_counter() - t0
@@ -843,7 +845,8 @@ def run_serving(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
             key = next_key[0]
             next_key[0] += 1
             t = srv.submit(A.rowptr, A.col, A.val * c, rng.uniform(-1, 1, A.n), TOL, key=key)
-            st, _, _, rr, _, _ = srv.wait(t)
+            _, ans = srv.wait_answer(t)
+            st = ans["status"]
             if st != 0:
                 raise RuntimeError(f"serving capacity request status {st}")
         service = (time.perf_counter() - t0) / cap_n
@@ -852,15 +855,28 @@ def run_serving(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
         if warmup:
             stream(servers, warmup, lam, "warmup")
         res, wall, new = stream(servers, n_requests, lam, "main")
-        lat = np.array([r[4] for r in res])
-        failed = sum(1 for r in res if r[0] != 0 or not (r[3] <= TOL))
+        lat = np.array([r["latency_ms"] for r in res])
+        failed = sum(1 for r in res if r["status"] != 0 or not (r["relres"] <= TOL))
+
+        def pct(key, rows):
+            v = np.array([r[key] for r in rows])
+            return {"p50": round(float(np.percentile(v, 50)), 2),
+                    "p99": round(float(np.percentile(v, 99)), 2)} if len(v) else None
+
+        parts = {k: pct(k, res) for k in ("queue_ms", "setup_ms", "solve_ms")}
+        by_size = {}
+        for lo, hi, name in ((0, 1e5, "below 1e5"), (1e5, 1e6, "1e5-1e6"), (1e6, 1e9, "above 1e6")):
+            rows = [r for r in res if lo <= r["n"] < hi]
+            if rows:
+                by_size[name] = {"requests": len(rows), "latency_ms": pct("latency_ms", rows)}
         sts = [sv.stats() for sv in servers]
         out.update({"lambda_per_s": round(lam, 2), "offered_load": load,
                     "new_matrix_fraction": round(new / n_requests, 3),
                     "p50_ms": round(float(np.percentile(lat, 50)), 2),
                     "p99_ms": round(float(np.percentile(lat, 99)), 2),
                     "solves_per_s": round(n_requests / wall, 2), "failed": failed,
-                    "batch_mean": round(float(np.mean([r[5] for r in res])), 2),
+                    "latency_parts": parts, "latency_by_size": by_size,
+                    "batch_mean": round(float(np.mean([r["batch"] for r in res])), 2),
                     "batches": sum(x["batches"] for x in sts),
                     "cache_hits": sum(x["cache_hits"] for x in sts),
                     "setups": sum(x["setups"] for x in sts),
@@ -868,13 +884,14 @@ def run_serving(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
         out["sweep"] = []
         for ld, cnt in sweep:
             r2, w2, _ = stream(servers, cnt, ld / service, f"sweep {ld}")
-            l2 = np.array([r[4] for r in r2])
+            l2 = np.array([r["latency_ms"] for r in r2])
             out["sweep"].append({"offered_load": ld, "requests": cnt,
                                  "lambda_per_s": round(ld / service, 2),
                                  "p50_ms": round(float(np.percentile(l2, 50)), 2),
                                  "p99_ms": round(float(np.percentile(l2, 99)), 2),
                                  "solves_per_s": round(cnt / w2, 2),
-                                 "failed": sum(1 for r in r2 if r[0] != 0 or not (r[3] <= TOL))})
+                                 "failed": sum(1 for r in r2 if r["status"] != 0 or
+                                               not (r["relres"] <= TOL))})
     finally:
         for s in servers:
             s.close()

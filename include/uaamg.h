@@ -241,6 +241,7 @@ typedef struct uaamg_stats {
     int64_t graph_nodes;  /* kernel nodes of one outer iteration in the last graph built */
     double opc;           /* operator complexity sum_l nnz_l / nnz_0 */
     double grid_complexity;
+    uint64_t device_bytes; /* device memory the handle holds now (hierarchy and workspace) */
 } uaamg_stats;
 int uaamg_get_stats(const uaamg_handle* h, uaamg_stats* s);
 
@@ -313,6 +314,15 @@ int uaamg_server_wait(uaamg_server* s, uint64_t ticket, double* x, int32_t* iter
  * UAAMG_ERR_CANCELLED.  A request already being solved (or answered) is not interrupted:
  * *cancelled = 0 and its wait returns its result.  The ticket stays valid until waited on. */
 int uaamg_server_cancel(uaamg_server* s, uint64_t ticket, int32_t* cancelled);
+/* The answer of a request, with its time split: latency = queue (submit until a worker
+ * took it) + setup (of its matrix, when the batch brought it; 0 for a cache hit) + solve
+ * (the batch's solve) + hand-over. */
+typedef struct uaamg_answer {
+    int32_t status, iters, batch, cache_hit;
+    double relres, latency_ms, queue_ms, setup_ms, solve_ms;
+} uaamg_answer;
+/* uaamg_server_wait that also fills *a (may be NULL); returns the request's status. */
+int uaamg_server_wait_answer(uaamg_server* s, uint64_t ticket, double* x, uaamg_answer* a);
 int uaamg_server_stats(uaamg_server* s, uint64_t* done, uint64_t* batches, uint64_t* cache_hits,
                        uint64_t* setups, uint64_t* rejected, int32_t* cached);
 /* Finishes the queued requests, joins the workers and frees every cached hierarchy. */

@@ -32,6 +32,7 @@ EXPORTS = [
     "uaamg_server_create", "uaamg_server_submit", "uaamg_server_poll", "uaamg_server_wait",
     "uaamg_server_stats", "uaamg_server_destroy", "uaamg_server_cancel",
     "uaamg_solve_batch", "uaamg_setup_batch", "uaamg_measure_fp64_fma",
+    "uaamg_server_wait_answer",
 ]
 
 
@@ -55,7 +56,13 @@ class uaamg_params(C.Structure):
 class uaamg_stats(C.Structure):
     _fields_ = [("setup_ms", C.c_double), ("solve_ms", C.c_double), ("launches", C.c_int64),
                 ("graph_nodes", C.c_int64), ("opc", C.c_double),
-                ("grid_complexity", C.c_double)]
+                ("grid_complexity", C.c_double), ("device_bytes", C.c_uint64)]
+
+
+class uaamg_answer(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("batch", C.c_int32),
+                ("cache_hit", C.c_int32), ("relres", C.c_double), ("latency_ms", C.c_double),
+                ("queue_ms", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
 
 
 class UaamgError(RuntimeError):
@@ -117,6 +124,7 @@ def lib() -> C.CDLL:
             "uaamg_solve_batch": (C.c_int, [P, I32, P, P, P, D, P, P, P]),
             "uaamg_setup_batch": (C.c_int, [I32, P, P, I32, P, P]),
             "uaamg_measure_fp64_fma": (C.c_int, [I32, C.POINTER(D)]),
+            "uaamg_server_wait_answer": (C.c_int, [P, U64, P, C.POINTER(uaamg_answer)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -447,6 +455,14 @@ class Server:
         c = C.c_int32(0)
         check(lib().uaamg_server_cancel(self._s, ticket, C.byref(c)), "uaamg_server_cancel")
         return bool(c.value)
+
+    def wait_answer(self, ticket: int):
+        """Returns (x, answer dict with status, iters, batch, cache_hit, relres, latency_ms,
+        queue_ms, setup_ms, solve_ms)."""
+        x = np.zeros(self._n.pop(ticket))
+        a = uaamg_answer()
+        lib().uaamg_server_wait_answer(self._s, ticket, x.ctypes.data, C.byref(a))
+        return x, {k: getattr(a, k) for k, _ in uaamg_answer._fields_}
 
     def stats(self) -> dict:
         v = [C.c_uint64() for _ in range(5)]

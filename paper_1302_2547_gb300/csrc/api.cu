@@ -314,6 +314,7 @@ int uaamg_get_stats(const uaamg_handle* hh, uaamg_stats* s) {
     }
     s->opc = z / (double)h->lev[0].nnz;
     s->grid_complexity = nn / (double)h->lev[0].n;
+    s->device_bytes = (uint64_t)h->bytes;
     return UAAMG_OK;
 }
 

@@ -44,14 +44,16 @@ struct Request {
     std::vector<double> x;
     int32_t status = -1, iters = 0, batch = 0, cache_hit = 0;
     double relres = 0.0, latency_ms = 0.0;
+    double queue_ms = 0.0, setup_ms = 0.0, solve_ms = 0.0;
     bool done = false;
 };
 
 struct CacheEntry {
     uint64_t key;
     uaamg_handle* h = nullptr;
-    uint64_t bytes = 0;
-    int users = 0;  // workers currently solving with it
+    uint64_t bytes = 0;  // device bytes counted against the budget: the handle's own once it
+                         // exists, plus what the batch using it reserved for its workspace
+    int users = 0;       // workers currently solving with it
     cudaStream_t stream = nullptr;
 };
 
@@ -133,11 +135,17 @@ struct uaamg_server {
 };
 
 // Device bytes a hierarchy of this matrix may take (level 0 plus coarse levels, smoother
-// data, setup scratch, and the solve workspace of up to `cols` right-hand sides): used for
-// admission before setup runs.
+// data, setup scratch, and the solve workspace of `cols` right-hand sides): an upper bound
+// used for admission before the setup or solve runs.
 static uint64_t estimate_bytes(const Matrix& A, int cols) {
     const uint64_t n = (uint64_t)A.n, z = (uint64_t)A.nnz;
     return 2 * (16 * z + 120 * n) + (uint64_t)cols * n * 96 + (64ULL << 20);
+}
+
+// The device bytes a handle holds now.
+static uint64_t handle_bytes(uaamg_handle* h) {
+    uaamg_stats st{};
+    return (h && uaamg_get_stats(h, &st) == UAAMG_OK) ? st.device_bytes : 0;
 }
 
 namespace {
@@ -183,8 +191,15 @@ void uaamg_server::worker_main(int wid) {
             // of one uaamg_solve_batch call
             double tol = 0.0;
             bool rejected = false, wait_memory = false;
-            uint64_t reserve = 0;  // bytes of the hierarchies this batch sets up
             std::unordered_map<uint64_t, size_t> gi;
+            // a group's entry counts at least the estimate for its columns so far
+            auto reserve = [&](CacheEntry* e, const Matrix& A, int R) {
+                const uint64_t need = estimate_bytes(A, R);
+                if (e->bytes >= need) return true;
+                if (!make_room(need - e->bytes)) return false;
+                e->bytes = need;
+                return true;
+            };
             for (auto it = queue.begin(); it != queue.end() && taken < max_batch;) {
                 std::shared_ptr<Request> q = *it;
                 const uint64_t key = q->A->key;
@@ -200,7 +215,7 @@ void uaamg_server::worker_main(int wid) {
                     Group g;
                     g.entry = find(key);
                     if (!g.entry) {
-                        const uint64_t need = estimate_bytes(*q->A, cols);
+                        const uint64_t need = estimate_bytes(*q->A, 1);
                         if (budget && need > budget) {  // can never fit: reject
                             q->status = UAAMG_ERR_BUDGET;
                             q->done = true;
@@ -209,20 +224,28 @@ void uaamg_server::worker_main(int wid) {
                             it = queue.erase(it);
                             continue;
                         }
-                        if (!make_room(reserve + need)) {
+                        if (!make_room(need)) {
                             if (taken == 0) wait_memory = true;
                             if (taken == 0) break;
                             ++it;
                             continue;
                         }
-                        reserve += need;
                         cache.push_front(CacheEntry{key, nullptr, need, 0, nullptr});
                         g.entry = &cache.front();
                         g.need_setup = true;
+                    } else if (!reserve(g.entry, *q->A, 1)) {
+                        if (taken == 0) wait_memory = true;
+                        if (taken == 0) break;
+                        ++it;
+                        continue;
                     }
                     g.entry->users++;
                     f = gi.emplace(key, groups.size()).first;
                     groups.push_back(std::move(g));
+                } else if (!reserve(groups[f->second].entry, *q->A,
+                                    (int)groups[f->second].reqs.size() + 1)) {
+                    ++it;  // no room for one more column of this matrix now
+                    continue;
                 }
                 Group& g = groups[f->second];
                 if (!g.need_setup) {
@@ -230,6 +253,8 @@ void uaamg_server::worker_main(int wid) {
                     n_hits++;
                 }
                 g.reqs.push_back(q);
+                q->queue_ms =
+                    std::chrono::duration<double, std::milli>(Clock::now() - q->t_submit).count();
                 tol = q->tol;
                 taken++;
                 it = queue.erase(it);
@@ -246,7 +271,10 @@ void uaamg_server::worker_main(int wid) {
             const Matrix& A = *g.reqs[0]->A;
             uaamg_csr csr{A.n, A.nnz, A.rowptr.data(), A.col.data(), A.val.data(), 0};
             uaamg_handle* h = nullptr;
+            const auto t0 = Clock::now();
             g.status = uaamg_setup(&csr, &params, stream, &h);
+            const double ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+            for (auto& q : g.reqs) q->setup_ms = ms;
             std::lock_guard<std::mutex> lk(mu);
             n_setups++;
             if (g.status != UAAMG_OK) {
@@ -284,6 +312,7 @@ void uaamg_server::worker_main(int wid) {
         its.assign(ncol, 0);
         rr.assign(ncol, 0.0);
         const double tol = taken ? groups[0].reqs[0]->tol : 1e-8;
+        const auto t_solve = Clock::now();
         if (ns == 1 && nr[0] == 1) {
             st = uaamg_solve(live[0]->entry->h, B[0].data(), X[0].data(), tol, 0, &its[0], &rr[0]);
         } else if (ns == 1) {
@@ -302,6 +331,7 @@ void uaamg_server::worker_main(int wid) {
                                    its.data(), rr.data(), stream);
         }
         const auto t_end = Clock::now();
+        const double solve_ms = std::chrono::duration<double, std::milli>(t_end - t_solve).count();
         std::lock_guard<std::mutex> lk(mu);
         size_t c = 0;
         for (int s = 0; s < ns; s++) {
@@ -317,8 +347,13 @@ void uaamg_server::worker_main(int wid) {
             }
         }
         for (Group& g : groups) {
-            if (g.entry) g.entry->users--;
+            if (g.entry) {
+                g.entry->users--;
+                // from now on the entry counts what its handle holds (below the estimate)
+                if (g.entry->h) g.entry->bytes = handle_bytes(g.entry->h);
+            }
             for (auto& q : g.reqs) {
+                q->solve_ms = solve_ms;
                 if (g.status != UAAMG_OK) q->status = g.status;
                 q->batch = taken;
                 q->latency_ms =
@@ -442,6 +477,29 @@ int uaamg_server_cancel(uaamg_server* s, uint64_t ticket, int32_t* cancelled) {
         break;
     }
     return UAAMG_OK;
+}
+
+int uaamg_server_wait_answer(uaamg_server* s, uint64_t ticket, double* x, uaamg_answer* a) {
+    if (!s) return UAAMG_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return UAAMG_ERR_INVALID_ARG;
+    std::shared_ptr<Request> req = it->second;
+    s->cv_done.wait(lk, [&] { return req->done; });
+    if (x && !req->x.empty()) memcpy(x, req->x.data(), sizeof(double) * req->x.size());
+    if (a) {
+        a->status = req->status;
+        a->iters = req->iters;
+        a->batch = req->batch;
+        a->cache_hit = req->cache_hit;
+        a->relres = req->relres;
+        a->latency_ms = req->latency_ms;
+        a->queue_ms = req->queue_ms;
+        a->setup_ms = req->setup_ms;
+        a->solve_ms = req->solve_ms;
+    }
+    s->tickets.erase(it);
+    return req->status;
 }
 
 int uaamg_server_stats(uaamg_server* s, uint64_t* done, uint64_t* batches, uint64_t* cache_hits,

@@ -112,7 +112,7 @@ def test_binding_structs_match_the_c_layout(tmp_path):
     from paper_1302_2547_gb300 import _lib as U
 
     structs = {"uaamg_csr": U.uaamg_csr, "uaamg_params": U.uaamg_params,
-               "uaamg_stats": U.uaamg_stats}
+               "uaamg_stats": U.uaamg_stats, "uaamg_answer": U.uaamg_answer}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "uaamg.h"',
              'int main(void) {']
     for cname, py in structs.items():
@@ -144,7 +144,7 @@ def test_binding_structs_have_every_header_field():
     text = open(os.path.join(ROOT, "include", "uaamg.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     for cname, py in (("uaamg_csr", U.uaamg_csr), ("uaamg_params", U.uaamg_params),
-                      ("uaamg_stats", U.uaamg_stats)):
+                      ("uaamg_stats", U.uaamg_stats), ("uaamg_answer", U.uaamg_answer)):
         body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (cname, cname), text, re.S).group(1)
         names = []
         for decl in body.split(";"):
