@@ -167,6 +167,7 @@ EAGER = False  # --eager: launch every kernel directly instead of replaying grap
 TMA_ROWS = None  # --tma-rows: levels of at least this many rows use the TMA-staged kernels
 FUSE_BELOW = None  # --fuse-below: levels of at most this many rows run the one-block cycle
 SELL_ROWS = None  # --sell-rows: levels of at least this many rows use the sliced ELLPACK copy
+CLUSTER_BELOW = None  # --cluster-below: levels of at most this many rows run on one cluster
 
 
 def bench_params(U, precision, profile_class=0):
@@ -175,6 +176,8 @@ def bench_params(U, precision, profile_class=0):
         extra["fuse_below"] = FUSE_BELOW
     if SELL_ROWS is not None:
         extra["sell_rows"] = SELL_ROWS
+    if CLUSTER_BELOW is not None:
+        extra["cluster_below"] = CLUSTER_BELOW
     return U.uaamg_default_params(precision=precision, profile_class=profile_class,
                                   use_graphs=0 if EAGER else 1, **BENCH_PARAMS, **extra)
 
@@ -1057,14 +1060,18 @@ def main():
                     help="row threshold of the TMA-staged row-block kernels (0 = off)")
     ap.add_argument("--fuse-below", type=int, default=None,
                     help="levels of at most this many rows run the one-block K-cycle (0 = off)")
+    ap.add_argument("--cluster-below", type=int, default=None,
+                    help="levels of at most this many rows run their K-cycle on one "
+                         "thread-block cluster (0 = off)")
     ap.add_argument("--sell-rows", type=int, default=None,
                     help="row threshold of the sliced ELLPACK level copies (0 = off)")
     args = ap.parse_args()
-    global EAGER, TMA_ROWS, FUSE_BELOW, SELL_ROWS
+    global EAGER, TMA_ROWS, FUSE_BELOW, SELL_ROWS, CLUSTER_BELOW
     EAGER = args.eager
     TMA_ROWS = args.tma_rows
     FUSE_BELOW = args.fuse_below
     SELL_ROWS = args.sell_rows
+    CLUSTER_BELOW = args.cluster_below
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
 

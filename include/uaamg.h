@@ -115,6 +115,11 @@ typedef struct uaamg_params {
                              relative 1e-9 count as equal (the split whose mask of the union's
                              ascending vertices is smallest wins).  A pair without such a split
                              stays as it is.  The number of aggregates does not change. */
+    int32_t cluster_below; /* coarse levels with at most this many unknowns run their K-cycle
+                              in one launch on one thread-block cluster (pre = post = 1 only;
+                              8 or 16 blocks that synchronise by cluster barriers and exchange
+                              inner products through distributed shared memory); 0 = off.
+                              Takes precedence over fuse_below. */
     int64_t wait_limit_ns; /* limit of every bounded device-side wait of this handle: a grid
                               barrier of a cooperative kernel, a wait for a bulk copy into
                               shared memory (measured in SM clock cycles, about 2 per ns).

@@ -148,6 +148,7 @@ struct Handle {
     size_t partials_cap = 0;
     // fused small-level K-cycle: first level handled by k_tail (0 = none)
     int tail_level = 0;
+    bool tail_cluster = false;  // the tail runs on a thread-block cluster (else one block)
     TailLevel* tail_dev = nullptr;
     // uaamg_solve_many workspace (sized for multi_R columns) and its iteration graph
     int multi_R = 0;

@@ -234,12 +234,295 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
     }
 }
 
+// ---- the same recursion on one thread-block cluster -------------------------------------
+// Levels up to cluster_below unknowns: the recursion runs on a cluster of kClusterCtas
+// blocks (one GPC), every block executing the same phase sequence on its share of the rows
+// (row i goes to thread i mod (blocks x threads)).  A phase ends with a cluster barrier
+// (release / acquire at cluster scope), so the next phase sees every block's writes;
+// vectors written inside the kernel are read through L2.  Inner products: each block sums
+// its rows in a fixed tree, publishes the partials in its shared memory, and after a
+// cluster barrier every block adds the blocks' partials in rank order from distributed
+// shared memory, so all blocks hold the same totals and take the same branches (the frame
+// stack is replicated per block).  The coarsest solve gives one warp per row across the
+// cluster.
+}  // namespace uaamg
+#include <cooperative_groups.h>
+namespace uaamg {
+namespace cg = cooperative_groups;
+
+constexpr int kClusterThreads = 512;
+
+template <typename T>
+__device__ __forceinline__ T ldg_cg(const T* p) {
+    return __ldcg(p);
+}
+
+// Cluster-wide fixed-order sum of ND values; every thread of every block receives the
+// totals.  `slot` alternates between two partial buffers, so a block that runs ahead cannot
+// overwrite partials another block is still reading.
+template <int ND>
+__device__ __forceinline__ void cluster_sum(double (&v)[ND], double (*part)[3], int slot) {
+    __shared__ double sh[ND][kClusterThreads / 32];
+    cg::cluster_group cl = cg::this_cluster();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+            double s = 0.0;
+            for (int w = 0; w < kClusterThreads / 32; w++) s += sh[k][w];
+            part[slot][k] = s;
+        }
+    }
+    cl.sync();
+    const unsigned nb = cl.num_blocks();
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+        double s = 0.0;
+        for (unsigned r = 0; r < nb; r++) s += cl.map_shared_rank(&part[slot][0], r)[k];
+        v[k] = s;
+    }
+}
+
+template <typename T, typename G>
+__device__ __forceinline__ T cl_row(const TailLevel& L, int i, G g) {
+    return tail_row<T>(L, i, g);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kClusterThreads, 1)
+k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double tau,
+               const int* skip) {
+    if (skip && *(volatile const int*)skip) return;  // uniform over the cluster
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ TailFrame st[kTailMaxFrames];
+    __shared__ int sp;
+    __shared__ double part[2][3];  // this block's inner-product partials (two slots)
+    int slot = 0;
+    const int G = (int)cl.num_blocks() * kClusterThreads;
+    const int g0 = (int)cl.block_rank() * kClusterThreads + threadIdx.x;
+    if (threadIdx.x == 0) {
+        st[0] = TailFrame{0, m0, 0, lv[m0].rhs, lv[m0].out, 0.0, 0.0, 0.0};
+        sp = 1;
+    }
+    __syncthreads();
+    while (true) {
+        const int top = sp;
+        if (top == 0) break;
+        const TailFrame f = st[top - 1];
+        __syncthreads();
+        const TailLevel& L = lv[f.level];
+        const T* in = (const T*)f.in;
+        T* out = (T*)f.out;
+        int push = 0, pop = 0, next_phase = f.phase;
+        TailFrame child{};
+        double rho1 = f.rho1, w1 = f.w1, w2 = f.w2;
+        if (f.kind == 0) {  // ---- K_m: two flexible-CG steps preconditioned by B_m ----
+            T *c1 = (T*)L.c1, *v1 = (T*)L.v1, *rt = (T*)L.rt, *c2 = (T*)L.c2, *v2 = (T*)L.v2;
+            if (f.level == nlev - 1) {  // exact solve with the dense inverse, a warp per row
+                const int lane = threadIdx.x & 31;
+                for (int i = g0 >> 5; i < L.n; i += G >> 5) {
+                    double sum = 0.0;
+                    for (int j = lane; j < L.n; j += 32)
+                        sum = fma(inv[(size_t)i * L.n + j], (double)ldg_cg(in + j), sum);
+                    sum = warp_sum(sum);
+                    if (lane == 0) out[i] = (T)sum;
+                }
+                pop = 1;
+            } else if (f.phase == 0) {  // c1 = B_m(rho)
+                child = TailFrame{1, f.level, 0, in, c1, 0.0, 0.0, 0.0};
+                push = 1;
+                next_phase = 1;
+            } else if (f.phase == 1) {  // v1 = A c1; rho1, alpha1; rho~
+                double d[3] = {0.0, 0.0, 0.0};
+                for (int i = g0; i < L.n; i += G) {
+                    const T acc = cl_row<T>(L, i, [&](int j) { return ldg_cg(c1 + j); });
+                    v1[i] = acc;
+                    const double xi = (double)ldg_cg(c1 + i);
+                    d[0] += xi * (double)acc;
+                    d[1] += xi * (double)ldg_cg(in + i);
+                }
+                cluster_sum<3>(d, part, slot);
+                slot ^= 1;
+                rho1 = d[0];
+                w1 = 0.0;
+                w2 = 0.0;
+                bool second = false;
+                if (rho1 > 0.0) {
+                    w1 = d[1] / rho1;
+                    second = (L.inner >= 2);
+                    if (second) {
+                        const T a1t = (T)w1;
+                        double nr[2] = {0.0, 0.0};
+                        for (int i = g0; i < L.n; i += G) {
+                            const T v = sub_rn(ldg_cg(in + i), mul_rn(a1t, v1[i]));
+                            rt[i] = v;
+                            nr[0] += (double)v * (double)v;
+                            nr[1] += (double)ldg_cg(in + i) * (double)ldg_cg(in + i);
+                        }
+                        if (tau > 0.0) {
+                            cluster_sum<2>(nr, part, slot);
+                            slot ^= 1;
+                            if (sqrt(nr[0]) <= tau * sqrt(nr[1])) second = false;
+                        }
+                    }
+                }
+                if (second) {  // c2 = B_m(rho~)
+                    child = TailFrame{1, f.level, 0, rt, c2, 0.0, 0.0, 0.0};
+                    push = 1;
+                    next_phase = 2;
+                } else {
+                    next_phase = 3;
+                }
+            } else if (f.phase == 2) {  // v2 = A c2; beta, gamma, alpha2
+                double d[3] = {0.0, 0.0, 0.0};
+                for (int i = g0; i < L.n; i += G) {
+                    const T acc = cl_row<T>(L, i, [&](int j) { return ldg_cg(c2 + j); });
+                    v2[i] = acc;
+                    const double xi = (double)ldg_cg(c2 + i);
+                    d[0] += xi * (double)acc;
+                    d[1] += xi * (double)ldg_cg(v1 + i);
+                    d[2] += xi * (double)ldg_cg(rt + i);
+                }
+                cluster_sum<3>(d, part, slot);
+                slot ^= 1;
+                const double beta = d[0], gamma = d[1], alpha2 = d[2];
+                const double rho2 = beta - gamma * gamma / rho1;
+                if (rho2 > 0.0) {
+                    w1 = w1 - gamma * alpha2 / (rho1 * rho2);
+                    w2 = alpha2 / rho2;
+                }
+                next_phase = 3;
+            } else {  // e = w1 c1 + w2 c2
+                const T w1t = (T)w1, w2t = (T)w2;
+                for (int i = g0; i < L.n; i += G) {
+                    T v = mul_rn(w1t, ldg_cg(c1 + i));
+                    if (w2 != 0.0) v = add_rn(v, mul_rn(w2t, ldg_cg(c2 + i)));
+                    out[i] = v;
+                }
+                pop = 1;
+            }
+        } else {  // ---- B_l: pre-sweep, restriction, K_{l+1}, prolongation + post-sweep ----
+            const TailLevel& C = lv[f.level + 1];
+            const T* minv = (const T*)L.minv;
+            T* x = (T*)L.w;
+            T* s = (T*)L.s;
+            T* rc = (T*)C.rhs;
+            T* ec = (T*)C.out;
+            if (f.phase == 0) {
+                for (int i = g0; i < L.n; i += G) {
+                    const T acc =
+                        cl_row<T>(L, i, [&](int j) { return mul_rn(minv[j], ldg_cg(in + j)); });
+                    x[i] = mul_rn(minv[i], ldg_cg(in + i));
+                    s[i] = sub_rn(ldg_cg(in + i), acc);
+                }
+                cl.sync();  // every block's s before the restriction
+                for (int I = g0; I < C.n; I += G) {
+                    const int q1 = L.aggptr[I + 1];
+                    T sum = T(0);
+                    for (int q = L.aggptr[I]; q < q1; q += kTailBatch) {
+                        T sv[kTailBatch];
+#pragma unroll
+                        for (int u = 0; u < kTailBatch; u++)
+                            sv[u] = q + u < q1 ? ldg_cg(s + L.members[q + u]) : T(0);
+#pragma unroll
+                        for (int u = 0; u < kTailBatch; u++)
+                            if (q + u < q1) sum = add_rn(sum, sv[u]);
+                    }
+                    rc[I] = sum;
+                }
+                child = TailFrame{0, f.level + 1, 0, rc, ec, 0.0, 0.0, 0.0};
+                push = 1;
+                next_phase = 1;
+            } else {
+                for (int i = g0; i < L.n; i += G) {
+                    const T acc = cl_row<T>(L, i, [&](int j) {
+                        return add_rn(ldg_cg(x + j), ldg_cg(ec + L.agg[j]));
+                    });
+                    const T xi = add_rn(ldg_cg(x + i), ldg_cg(ec + L.agg[i]));
+                    out[i] = add_rn(xi, mul_rn(minv[i], sub_rn(ldg_cg(in + i), acc)));
+                }
+                pop = 1;
+            }
+        }
+        cl.sync();  // this phase's writes are visible to every block of the cluster
+        if (threadIdx.x == 0) {
+            if (pop) {
+                sp = top - 1;
+            } else {
+                st[top - 1].phase = next_phase;
+                st[top - 1].rho1 = rho1;
+                st[top - 1].w1 = w1;
+                st[top - 1].w2 = w2;
+                if (push) {
+                    st[top] = child;
+                    sp = top + 1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Blocks of the cluster: 16 where the device allows that size for this kernel, else 8.
+template <typename T>
+static int cluster_blocks(Handle* h) {
+    static DevCache cache;
+    int c = cache.get(h->device);
+    if (c) return c;
+    c = 8;
+    if (cudaFuncSetAttribute(k_tail_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             1) == cudaSuccess) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(kClusterThreads);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_tail_cluster<T>, &cfg) == cudaSuccess &&
+            nclusters >= 1)
+            c = 16;
+    }
+    cudaGetLastError();
+    cache.set(h->device, c);
+    return c;
+}
+
 template <typename T>
 int launch_tail(Handle* h, int m0) {
-    k_tail<T><<<1, kTailThreads, 0, h->work>>>(h->tail_dev, m0, h->nlev, h->coarse_inv,
-                                               h->p.kcycle_tau, &h->ctrl->skip);
+    if (!h->tail_cluster) {
+        k_tail<T><<<1, kTailThreads, 0, h->work>>>(h->tail_dev, m0, h->nlev, h->coarse_inv,
+                                                   h->p.kcycle_tau, &h->ctrl->skip);
+        count_launch(h);
+        return check_cuda(cudaGetLastError());
+    }
+    const int nb = cluster_blocks<T>(h);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.stream = h->work;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = nb;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tail_cluster<T>, (const TailLevel*)h->tail_dev,
+                                       m0, h->nlev, (const double*)h->coarse_inv,
+                                       h->p.kcycle_tau, (const int*)&h->ctrl->skip);
     count_launch(h);
-    return check_cuda(cudaGetLastError());
+    return check_cuda(e);
 }
 template int launch_tail<float>(Handle*, int);
 template int launch_tail<double>(Handle*, int);

@@ -4,6 +4,8 @@
 // only reads back, per level, the pass count, n_c and nnz_c to size the next level.
 #include <string.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kern_sra.cuh"
 #include "kernels.cuh"
@@ -349,12 +351,14 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
     }
     {  // levels small enough for the fused K-cycle kernel (one pre- and post-sweep only)
         int m0 = 0;
+        const int below = std::max(h->p.fuse_below, h->p.cluster_below);
         if (h->p.pre == 1 && h->p.post == 1)
             for (int l = 1; l < h->nlev - 1; l++)
-                if (h->lev[l].n <= h->p.fuse_below) {
+                if (h->lev[l].n <= below) {
                     m0 = l;
                     break;
                 }
+        h->tail_cluster = m0 > 0 && h->lev[m0].n <= h->p.cluster_below;
         if (m0 > 0 && st == UAAMG_OK) {
             std::vector<TailLevel> tl(h->nlev);
             for (int l = 0; l < h->nlev; l++) {
