@@ -224,6 +224,90 @@ template int launch_restrict<float>(Handle*, int, const int*, const int*, const 
 template int launch_restrict<double>(Handle*, int, const int*, const int*, const double*, double*, const int*);
 
 // ---------------------------------------------------------------------------------------
+// The first sweep fused with the restriction (Sections 4.1, 4.2): for every aggregate I,
+// x_j = Minv_j r_j for its members j and r_c[I] = sum_j (r_j - (A x)_j), members in
+// ascending order, so the residual s = r - A x is never stored.  One warp per aggregate,
+// one lane per member (32 at a time); each lane adds its row in stored order with fused
+// multiply-adds, eight entries' loads issued together, and lane 0 adds the members'
+// residuals in order.  With RT, r = rho~ = rho - a1 v1 is formed on the fly and stored in
+// `y3` (as RB_PRE1_RT).
+// ---------------------------------------------------------------------------------------
+template <typename T, bool RT>
+__global__ void __launch_bounds__(kThreads) k_pre1_restrict(RBArgs<T> a, int nc,
+                                                            const int* __restrict__ aggptr,
+                                                            const int* __restrict__ members,
+                                                            T* __restrict__ rc) {
+    pdl_wait();
+    pdl_trigger();
+    if (a.skip && *(volatile const int*)a.skip) return;
+    const int lane = threadIdx.x & 31;
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (I >= nc) return;  // whole warps leave together
+    T a1 = T(0);
+    if constexpr (RT) a1 = sizeof(T) == 4 ? (T)a.rsc->a1f : (T)a.rsc->a1;
+    auto rin = [&](int j) -> T {
+        if constexpr (RT) return sub_rn(a.r[j], mul_rn(a1, a.d1[j]));
+        else return a.r[j];
+    };
+    const int q0 = aggptr[I], q1 = aggptr[I + 1];
+    T sum = T(0);
+    for (int qb = q0; qb < q1; qb += 32) {
+        const int q = qb + lane;
+        T sj = T(0);
+        if (q < q1) {
+            const int j = members[q];
+            const T rj = rin(j);
+            const int k1 = a.rowptr[j + 1];
+            T acc = T(0);
+            for (int k = a.rowptr[j]; k < k1; k += 8) {
+                int jj[8];
+                T vv[8], xg[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const bool in = k + u < k1;
+                    jj[u] = in ? a.col[k + u] : 0;
+                    vv[u] = in ? a.val[k + u] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u++)
+                    xg[u] = (k + u < k1) ? mul_rn(a.minv[jj[u]], rin(jj[u])) : T(0);
+#pragma unroll
+                for (int u = 0; u < 8; u++)
+                    if (k + u < k1) acc = fma_rn(vv[u], xg[u], acc);
+            }
+            a.y[j] = mul_rn(a.minv[j], rj);
+            if constexpr (RT) a.y3[j] = rj;
+            sj = sub_rn(rj, acc);
+        }
+        const int cnt = min(32, q1 - qb);
+        for (int u = 0; u < cnt; u++) {
+            const T v = __shfl_sync(0xffffffffu, sj, u);
+            if (lane == 0) sum = add_rn(sum, v);
+        }
+    }
+    if (lane == 0) rc[I] = sum;
+}
+
+template <typename T>
+int launch_pre1_restrict(Handle* h, int mode, const RBArgs<T>& a, int nc, const int* aggptr,
+                         const int* members, T* rc) {
+    const int grid = grid_for((long long)nc * 32, kThreads);
+    cudaError_t e;
+    if (mode == RB_PRE1_RT)
+        e = launch_k(a.n <= kPdlMaxRows, k_pre1_restrict<T, true>, dim3(grid), dim3(kThreads), 0,
+                     h->work, a, nc, aggptr, members, rc);
+    else
+        e = launch_k(a.n <= kPdlMaxRows, k_pre1_restrict<T, false>, dim3(grid), dim3(kThreads), 0,
+                     h->work, a, nc, aggptr, members, rc);
+    count_launch(h);
+    return check_cuda(e);
+}
+template int launch_pre1_restrict<float>(Handle*, int, const RBArgs<float>&, int, const int*,
+                                         const int*, float*);
+template int launch_pre1_restrict<double>(Handle*, int, const RBArgs<double>&, int, const int*,
+                                          const int*, double*);
+
+// ---------------------------------------------------------------------------------------
 // Coarsest solve: out = A_c^{-1} in with the precomputed dense inverse (warp per row, FP64).
 // ---------------------------------------------------------------------------------------
 template <typename T>

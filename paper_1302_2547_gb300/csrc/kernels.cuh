@@ -284,6 +284,10 @@ int build_sell(Handle* h, Level& L, bool mixed);
 template <typename T>
 int launch_restrict(Handle* h, int nc, const int* aggptr, const int* members, const T* s,
                     T* rc, const int* skip);
+// RB_PRE1 / RB_PRE1_RT fused with the restriction of s = r - A x (s is not stored)
+template <typename T>
+int launch_pre1_restrict(Handle* h, int mode, const RBArgs<T>& a, int nc, const int* aggptr,
+                         const int* members, T* rc);
 template <typename T>
 int launch_dense_apply(Handle* h, int n, const double* inv, const T* in, T* out,
                        const int* skip);

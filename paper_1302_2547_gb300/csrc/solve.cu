@@ -141,8 +141,13 @@ static int apply_B(Handle* h, int l, const T* in, T* out, const RtFuse<T>* rf = 
             a.rsc = rf->sc;
             a.y3 = const_cast<T*>(in);
         }
+        // levels of the row-block kernels with one pre-sweep: the sweep and the restriction
+        // in one launch (the large levels keep the bandwidth-tuned sweep and restrict apart)
+        const bool fused = pre == 1 && !a.sptr && !(h->p.tma_rows > 0 && L.n >= h->p.tma_rows);
         int ps = prof_begin(h, UAAMG_KCLASS_SMOOTH0, l);
-        if ((st = launch_rowblock<T>(h, mode, 0, a))) return st;
+        if (fused) st = launch_pre1_restrict<T>(h, mode, a, L.nc, L.aggptr, L.members, rc);
+        else st = launch_rowblock<T>(h, mode, 0, a);
+        if (st) return st;
         prof_end(h, ps);
         x = y;
         for (int i = 1; i < pre; i++) {
@@ -161,7 +166,8 @@ static int apply_B(Handle* h, int l, const T* in, T* out, const RtFuse<T>* rf = 
             c.y = s;
             if ((st = launch_rowblock<T>(h, RB_RESID, 0, c))) return st;
         }
-        if ((st = launch_restrict<T>(h, L.nc, L.aggptr, L.members, s, rc, skip))) return st;
+        if (!fused && (st = launch_restrict<T>(h, L.nc, L.aggptr, L.members, s, rc, skip)))
+            return st;
     } else {
         if ((st = launch_restrict<T>(h, L.nc, L.aggptr, L.members, in, rc, skip))) return st;
         if ((st = launch_copy<T>(h, L.n, nullptr, s, skip))) return st;  // x = 0
