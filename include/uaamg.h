@@ -115,6 +115,11 @@ typedef struct uaamg_params {
                              relative 1e-9 count as equal (the split whose mask of the union's
                              ascending vertices is smallest wins).  A pair without such a split
                              stays as it is.  The number of aggregates does not change. */
+    int32_t restrict_fuse_below; /* levels with at most this many unknowns (on the row-block
+                                    kernels, one pre-sweep) run their first sweep and the
+                                    restriction in one launch, a warp per aggregate; 0 = never
+                                    (default: on GB300 the two launches are faster except on
+                                    hierarchies of a few thousand unknowns) */
     int32_t cluster_below; /* coarse levels with at most this many unknowns run their K-cycle
                               in one launch on one thread-block cluster (pre = post = 1 only;
                               8 or 16 blocks that synchronise by cluster barriers and exchange

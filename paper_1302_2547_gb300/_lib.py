@@ -50,7 +50,8 @@ class uaamg_params(C.Structure):
                 ("agg_repeat", C.c_int32), ("kcycle_ratio", C.c_double),
                 ("min_coarsening", C.c_double), ("jacobi_omega", C.c_double),
                 ("tma_rows", C.c_int32), ("sell_rows", C.c_int32), ("fuse_below", C.c_int32),
-                ("sra_rounds", C.c_int32), ("cluster_below", C.c_int32),
+                ("sra_rounds", C.c_int32), ("restrict_fuse_below", C.c_int32),
+                ("cluster_below", C.c_int32),
                 ("wait_limit_ns", C.c_int64)]
 
 

@@ -78,7 +78,7 @@ static bool params_ok(const uaamg_params* p) {
            (p->agg_repeat == 1 || p->agg_repeat == 2) && p->kcycle_ratio >= 0.0 &&
            p->min_coarsening >= 0.0 && p->fuse_below >= 0 && p->jacobi_omega >= 0.0 &&
            p->tma_rows >= 0 && p->sell_rows >= 0 && p->sra_rounds >= 0 && p->sra_rounds <= 64 &&
-           p->wait_limit_ns >= 0 && p->cluster_below >= 0;
+           p->wait_limit_ns >= 0 && p->cluster_below >= 0 && p->restrict_fuse_below >= 0;
 }
 
 }  // namespace uaamg
@@ -111,6 +111,7 @@ void uaamg_default_params(uaamg_params* p) {
     p->sell_rows = 0;
     p->fuse_below = 0;
     p->sra_rounds = 0;
+    p->restrict_fuse_below = 0;
     p->cluster_below = 0;
     p->wait_limit_ns = 0;
 }

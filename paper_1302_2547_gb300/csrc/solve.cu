@@ -143,7 +143,8 @@ static int apply_B(Handle* h, int l, const T* in, T* out, const RtFuse<T>* rf = 
         }
         // levels of the row-block kernels with one pre-sweep: the sweep and the restriction
         // in one launch (the large levels keep the bandwidth-tuned sweep and restrict apart)
-        const bool fused = pre == 1 && !a.sptr && !(h->p.tma_rows > 0 && L.n >= h->p.tma_rows);
+        const bool fused = pre == 1 && !a.sptr && L.n <= h->p.restrict_fuse_below &&
+                           !(h->p.tma_rows > 0 && L.n >= h->p.tma_rows);
         int ps = prof_begin(h, UAAMG_KCLASS_SMOOTH0, l);
         if (fused) st = launch_pre1_restrict<T>(h, mode, a, L.nc, L.aggptr, L.members, rc);
         else st = launch_rowblock<T>(h, mode, 0, a);
