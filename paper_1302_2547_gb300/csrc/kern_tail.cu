@@ -92,6 +92,8 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
     if (skip && *(volatile const int*)skip) return;
     __shared__ TailFrame st[kTailMaxFrames];
     __shared__ int sp;
+    __shared__ double s_w;  // a step scalar computed by thread 0
+    __shared__ int s_flag;  // a step decision taken by thread 0
     if (threadIdx.x == 0) {
         st[0] = TailFrame{0, m0, 0, lv[m0].rhs, lv[m0].out, 0.0, 0.0, 0.0};
         sp = 1;
@@ -102,7 +104,9 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
         if (top == 0) break;
         const TailFrame f = st[top - 1];
         __syncthreads();
-        const TailLevel& L = lv[f.level];
+        // the level's descriptor by value: its pointers stay in registers (through a
+        // reference every store to a vector could alias them, so each use reloads them)
+        const TailLevel L = lv[f.level];
         const T* in = (const T*)f.in;
         T* out = (T*)f.out;
         int push = 0, pop = 0, next_phase = f.phase;
@@ -128,25 +132,30 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
                 double d[3] = {0.0, 0.0, 0.0};
                 spmv_rows<T>(L, c1, v1, 2, in, nullptr, d);
                 block_sum<3>(d);
-                rho1 = d[0];
-                w1 = 0.0;
-                w2 = 0.0;
-                bool second = false;
-                if (rho1 > 0.0) {
-                    w1 = d[1] / rho1;
-                    second = (L.inner >= 2);
-                    if (second) {
-                        const T a1t = (T)w1;
-                        double nr[2] = {0.0, 0.0};
-                        for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
-                            const T v = sub_rn(in[i], mul_rn(a1t, v1[i]));
-                            rt[i] = v;
-                            nr[0] += (double)v * (double)v;
-                            nr[1] += (double)in[i] * (double)in[i];
-                        }
-                        block_sum<2>(nr);
-                        if (tau > 0.0 && sqrt(nr[0]) <= tau * sqrt(nr[1])) second = false;
+                // the step's scalars in one thread, broadcast through shared memory
+                if (threadIdx.x == 0) {
+                    rho1 = d[0];
+                    w1 = rho1 > 0.0 ? d[1] / rho1 : 0.0;
+                    w2 = 0.0;
+                    s_w = w1;
+                    s_flag = (rho1 > 0.0 && L.inner >= 2) ? 1 : 0;
+                }
+                __syncthreads();
+                bool second = s_flag != 0;
+                if (second) {
+                    const T a1t = (T)s_w;
+                    double nr[2] = {0.0, 0.0};
+                    for (int i = threadIdx.x; i < L.n; i += kTailThreads) {
+                        const T v = sub_rn(in[i], mul_rn(a1t, v1[i]));
+                        rt[i] = v;
+                        nr[0] += (double)v * (double)v;
+                        nr[1] += (double)in[i] * (double)in[i];
                     }
+                    block_sum<2>(nr);
+                    if (threadIdx.x == 0)
+                        s_flag = (tau > 0.0 && sqrt(nr[0]) <= tau * sqrt(nr[1])) ? 0 : 1;
+                    __syncthreads();
+                    second = s_flag != 0;
                 }
                 if (second) {  // c2 = B_m(rho~)
                     child = TailFrame{1, f.level, 0, rt, c2, 0.0, 0.0, 0.0};
@@ -159,11 +168,13 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
                 double d[3] = {0.0, 0.0, 0.0};
                 spmv_rows<T>(L, c2, v2, 3, v1, rt, d);
                 block_sum<3>(d);
-                const double beta = d[0], gamma = d[1], alpha2 = d[2];
-                const double rho2 = beta - gamma * gamma / rho1;
-                if (rho2 > 0.0) {
-                    w1 = w1 - gamma * alpha2 / (rho1 * rho2);
-                    w2 = alpha2 / rho2;
+                if (threadIdx.x == 0) {  // only thread 0 keeps the frame's scalars
+                    const double beta = d[0], gamma = d[1], alpha2 = d[2];
+                    const double rho2 = beta - gamma * gamma / rho1;
+                    if (rho2 > 0.0) {
+                        w1 = w1 - gamma * alpha2 / (rho1 * rho2);
+                        w2 = alpha2 / rho2;
+                    }
                 }
                 next_phase = 3;
             } else {  // e = w1 c1 + w2 c2
@@ -176,7 +187,7 @@ k_tail(const TailLevel* lv, int m0, int nlev, const double* inv, double tau, con
                 pop = 1;
             }
         } else {  // ---- B_l: pre-sweep, restriction, K_{l+1}, prolongation + post-sweep ----
-            const TailLevel& C = lv[f.level + 1];
+            const TailLevel C = lv[f.level + 1];
             const T* minv = (const T*)L.minv;
             T* x = (T*)L.w;
             T* s = (T*)L.s;
@@ -259,10 +270,13 @@ __device__ __forceinline__ T ldg_cg(const T* p) {
 
 // Cluster-wide fixed-order sum of ND values; every thread of every block receives the
 // totals.  `slot` alternates between two partial buffers, so a block that runs ahead cannot
-// overwrite partials another block is still reading.
+// overwrite partials another block is still reading.  One warp per block fetches the
+// blocks' partials from distributed shared memory (lane r reads block r's, all loads in
+// flight together) and adds them in rank order.
 template <int ND>
 __device__ __forceinline__ void cluster_sum(double (&v)[ND], double (*part)[3], int slot) {
     __shared__ double sh[ND][kClusterThreads / 32];
+    __shared__ double tot[ND];
     cg::cluster_group cl = cg::this_cluster();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -280,13 +294,22 @@ __device__ __forceinline__ void cluster_sum(double (&v)[ND], double (*part)[3], 
         }
     }
     cl.sync();
-    const unsigned nb = cl.num_blocks();
+    if (wid == 0) {
+        const int nb = (int)cl.num_blocks();
+        double pv[ND];
 #pragma unroll
-    for (int k = 0; k < ND; k++) {
-        double s = 0.0;
-        for (unsigned r = 0; r < nb; r++) s += cl.map_shared_rank(&part[slot][0], r)[k];
-        v[k] = s;
+        for (int k = 0; k < ND; k++)
+            pv[k] = lane < nb ? cl.map_shared_rank(&part[slot][0], lane)[k] : 0.0;
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+            double s = 0.0;
+            for (int r = 0; r < nb; r++) s += __shfl_sync(0xffffffffu, pv[k], r);
+            if (lane == 0) tot[k] = s;
+        }
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ND; k++) v[k] = tot[k];
 }
 
 template <typename T, typename G>
@@ -303,6 +326,8 @@ k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double 
     __shared__ TailFrame st[kTailMaxFrames];
     __shared__ int sp;
     __shared__ double part[2][3];  // this block's inner-product partials (two slots)
+    __shared__ double s_w;         // a step scalar computed by thread 0
+    __shared__ int s_flag;         // a step decision taken by thread 0
     int slot = 0;
     const int G = (int)cl.num_blocks() * kClusterThreads;
     const int g0 = (int)cl.block_rank() * kClusterThreads + threadIdx.x;
@@ -316,7 +341,9 @@ k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double 
         if (top == 0) break;
         const TailFrame f = st[top - 1];
         __syncthreads();
-        const TailLevel& L = lv[f.level];
+        // the level's descriptor by value: its pointers stay in registers (through a
+        // reference every store to a vector could alias them, so each use reloads them)
+        const TailLevel L = lv[f.level];
         const T* in = (const T*)f.in;
         T* out = (T*)f.out;
         int push = 0, pop = 0, next_phase = f.phase;
@@ -344,32 +371,37 @@ k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double 
                     const T acc = cl_row<T>(L, i, [&](int j) { return ldg_cg(c1 + j); });
                     v1[i] = acc;
                     const double xi = (double)ldg_cg(c1 + i);
-                    d[0] += xi * (double)acc;
-                    d[1] += xi * (double)ldg_cg(in + i);
+                    d[0] = fma(xi, (double)acc, d[0]);
+                    d[1] = fma(xi, (double)ldg_cg(in + i), d[1]);
                 }
                 cluster_sum<3>(d, part, slot);
                 slot ^= 1;
-                rho1 = d[0];
-                w1 = 0.0;
-                w2 = 0.0;
-                bool second = false;
-                if (rho1 > 0.0) {
-                    w1 = d[1] / rho1;
-                    second = (L.inner >= 2);
-                    if (second) {
-                        const T a1t = (T)w1;
-                        double nr[2] = {0.0, 0.0};
-                        for (int i = g0; i < L.n; i += G) {
-                            const T v = sub_rn(ldg_cg(in + i), mul_rn(a1t, v1[i]));
-                            rt[i] = v;
-                            nr[0] += (double)v * (double)v;
-                            nr[1] += (double)ldg_cg(in + i) * (double)ldg_cg(in + i);
-                        }
-                        if (tau > 0.0) {
-                            cluster_sum<2>(nr, part, slot);
-                            slot ^= 1;
-                            if (sqrt(nr[0]) <= tau * sqrt(nr[1])) second = false;
-                        }
+                // the step's scalars in one thread (FP64 divisions are costly on GB300's
+                // FP64 units when every thread repeats them), broadcast through shared memory
+                if (threadIdx.x == 0) {
+                    rho1 = d[0];
+                    w1 = rho1 > 0.0 ? d[1] / rho1 : 0.0;
+                    w2 = 0.0;
+                    s_w = w1;
+                    s_flag = (rho1 > 0.0 && L.inner >= 2) ? 1 : 0;
+                }
+                __syncthreads();
+                bool second = s_flag != 0;
+                if (second) {
+                    const T a1t = (T)s_w;
+                    double nr[2] = {0.0, 0.0};
+                    for (int i = g0; i < L.n; i += G) {
+                        const T v = sub_rn(ldg_cg(in + i), mul_rn(a1t, v1[i]));
+                        rt[i] = v;
+                        nr[0] += (double)v * (double)v;
+                        nr[1] += (double)ldg_cg(in + i) * (double)ldg_cg(in + i);
+                    }
+                    if (tau > 0.0) {
+                        cluster_sum<2>(nr, part, slot);
+                        slot ^= 1;
+                        if (threadIdx.x == 0) s_flag = (sqrt(nr[0]) <= tau * sqrt(nr[1])) ? 0 : 1;
+                        __syncthreads();
+                        second = s_flag != 0;
                     }
                 }
                 if (second) {  // c2 = B_m(rho~)
@@ -385,17 +417,19 @@ k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double 
                     const T acc = cl_row<T>(L, i, [&](int j) { return ldg_cg(c2 + j); });
                     v2[i] = acc;
                     const double xi = (double)ldg_cg(c2 + i);
-                    d[0] += xi * (double)acc;
-                    d[1] += xi * (double)ldg_cg(v1 + i);
-                    d[2] += xi * (double)ldg_cg(rt + i);
+                    d[0] = fma(xi, (double)acc, d[0]);
+                    d[1] = fma(xi, (double)ldg_cg(v1 + i), d[1]);
+                    d[2] = fma(xi, (double)ldg_cg(rt + i), d[2]);
                 }
                 cluster_sum<3>(d, part, slot);
                 slot ^= 1;
-                const double beta = d[0], gamma = d[1], alpha2 = d[2];
-                const double rho2 = beta - gamma * gamma / rho1;
-                if (rho2 > 0.0) {
-                    w1 = w1 - gamma * alpha2 / (rho1 * rho2);
-                    w2 = alpha2 / rho2;
+                if (threadIdx.x == 0) {  // only thread 0 keeps the frame's scalars
+                    const double beta = d[0], gamma = d[1], alpha2 = d[2];
+                    const double rho2 = beta - gamma * gamma / rho1;
+                    if (rho2 > 0.0) {
+                        w1 = w1 - gamma * alpha2 / (rho1 * rho2);
+                        w2 = alpha2 / rho2;
+                    }
                 }
                 next_phase = 3;
             } else {  // e = w1 c1 + w2 c2
@@ -408,7 +442,7 @@ k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double 
                 pop = 1;
             }
         } else {  // ---- B_l: pre-sweep, restriction, K_{l+1}, prolongation + post-sweep ----
-            const TailLevel& C = lv[f.level + 1];
+            const TailLevel C = lv[f.level + 1];
             const T* minv = (const T*)L.minv;
             T* x = (T*)L.w;
             T* s = (T*)L.s;
