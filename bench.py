@@ -168,6 +168,7 @@ TMA_ROWS = None  # --tma-rows: levels of at least this many rows use the TMA-sta
 FUSE_BELOW = None  # --fuse-below: levels of at most this many rows run the one-block cycle
 SELL_ROWS = None  # --sell-rows: levels of at least this many rows use the sliced ELLPACK copy
 CLUSTER_BELOW = None  # --cluster-below: levels of at most this many rows run on one cluster
+AUTOTUNE = None  # --autotune 0/1: time the kernel families per level at setup
 
 
 def bench_params(U, precision, profile_class=0):
@@ -178,6 +179,8 @@ def bench_params(U, precision, profile_class=0):
         extra["sell_rows"] = SELL_ROWS
     if CLUSTER_BELOW is not None:
         extra["cluster_below"] = CLUSTER_BELOW
+    if AUTOTUNE is not None:
+        extra["autotune"] = AUTOTUNE
     return U.uaamg_default_params(precision=precision, profile_class=profile_class,
                                   use_graphs=0 if EAGER else 1, **BENCH_PARAMS, **extra)
 
@@ -218,6 +221,9 @@ def run_gpu(args, rank, world):
             s = U.uaamg_get_stats(h)
             s["levels"] = U.uaamg_num_levels(h)
             s["coarsest_n"] = U.uaamg_level_info(h, s["levels"] - 1)[0]
+            s["kernels"] = [dict(level=l, n=U.uaamg_level_info(h, l)[0],
+                                 **U.uaamg_level_kernel(h, l))
+                            for l in range(s["levels"] - 1)]
             prof = U.uaamg_get_profile(h) if profile_class else None
             return it, rr, s, prof
         finally:
@@ -380,6 +386,13 @@ def run_gpu(args, rank, world):
                        "p99": round(float(np.percentile(lat, 99)), 3)},
         "iterations": int(np.median(its)), "relres_host_fp64": relres_host,
         "levels": stats["levels"], "coarsest_n": stats["coarsest_n"],
+        "level_kernels": [{"level": k["level"], "n": k["n"],
+                           "kernel": ["row-block", "TMA", "ELLPACK"][k["path"]],
+                           "rows_per_block": k["rows"],
+                           **({"tuned_us": dict(zip(["rb256", "rb128", "rb64", "rb32", "tma",
+                                                      "ellpack"], k["tune_us"]))}
+                              if k["tune_us"][0] > 0 else {})}
+                          for k in stats["kernels"] if k["n"] >= 32768],
         "opc": round(stats["opc"], 3),
         "grid_complexity": round(stats["grid_complexity"], 3),
         "plain_fp64": None if not p_rec else {
@@ -1060,18 +1073,21 @@ def main():
                     help="row threshold of the TMA-staged row-block kernels (0 = off)")
     ap.add_argument("--fuse-below", type=int, default=None,
                     help="levels of at most this many rows run the one-block K-cycle (0 = off)")
+    ap.add_argument("--autotune", type=int, default=None, choices=[0, 1],
+                    help="time the kernel families per level at setup (1) or not (0)")
     ap.add_argument("--cluster-below", type=int, default=None,
                     help="levels of at most this many rows run their K-cycle on one "
                          "thread-block cluster (0 = off)")
     ap.add_argument("--sell-rows", type=int, default=None,
                     help="row threshold of the sliced ELLPACK level copies (0 = off)")
     args = ap.parse_args()
-    global EAGER, TMA_ROWS, FUSE_BELOW, SELL_ROWS, CLUSTER_BELOW
+    global EAGER, TMA_ROWS, FUSE_BELOW, SELL_ROWS, CLUSTER_BELOW, AUTOTUNE
     EAGER = args.eager
     TMA_ROWS = args.tma_rows
     FUSE_BELOW = args.fuse_below
     SELL_ROWS = args.sell_rows
     CLUSTER_BELOW = args.cluster_below
+    AUTOTUNE = args.autotune
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
 

@@ -32,7 +32,7 @@ EXPORTS = [
     "uaamg_server_create", "uaamg_server_submit", "uaamg_server_poll", "uaamg_server_wait",
     "uaamg_server_stats", "uaamg_server_destroy", "uaamg_server_cancel",
     "uaamg_solve_batch", "uaamg_setup_batch", "uaamg_measure_fp64_fma",
-    "uaamg_server_wait_answer",
+    "uaamg_server_wait_answer", "uaamg_level_kernel",
 ]
 
 
@@ -51,7 +51,7 @@ class uaamg_params(C.Structure):
                 ("min_coarsening", C.c_double), ("jacobi_omega", C.c_double),
                 ("tma_rows", C.c_int32), ("sell_rows", C.c_int32), ("fuse_below", C.c_int32),
                 ("sra_rounds", C.c_int32), ("restrict_fuse_below", C.c_int32),
-                ("cluster_below", C.c_int32),
+                ("autotune", C.c_int32), ("cluster_below", C.c_int32),
                 ("wait_limit_ns", C.c_int64)]
 
 
@@ -127,6 +127,7 @@ def lib() -> C.CDLL:
             "uaamg_setup_batch": (C.c_int, [I32, P, P, I32, P, P]),
             "uaamg_measure_fp64_fma": (C.c_int, [I32, C.POINTER(D)]),
             "uaamg_server_wait_answer": (C.c_int, [P, U64, P, C.POINTER(uaamg_answer)]),
+            "uaamg_level_kernel": (C.c_int, [P, I32, C.POINTER(I32), C.POINTER(I32), P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -305,6 +306,16 @@ def uaamg_get_pass_of(h, l: int) -> np.ndarray:
     a = np.empty(n, np.int32)
     check(lib().uaamg_get_pass_of(h, l, a.ctypes.data), "uaamg_get_pass_of")
     return a
+
+
+def uaamg_level_kernel(h, l: int) -> dict:
+    """{"path": 0 row-block / 1 TMA / 2 ELLPACK, "rows": rows per block, "tune_us": the
+    autotuner's six first-sweep timings (-1 = not timed)}."""
+    p, r = C.c_int32(), C.c_int32()
+    us = np.zeros(6)
+    check(lib().uaamg_level_kernel(h, l, C.byref(p), C.byref(r), us.ctypes.data),
+          "uaamg_level_kernel")
+    return {"path": p.value, "rows": r.value, "tune_us": [round(float(u), 2) for u in us]}
 
 
 def uaamg_get_minv(h, l: int) -> np.ndarray:

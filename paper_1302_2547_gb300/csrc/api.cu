@@ -78,7 +78,8 @@ static bool params_ok(const uaamg_params* p) {
            (p->agg_repeat == 1 || p->agg_repeat == 2) && p->kcycle_ratio >= 0.0 &&
            p->min_coarsening >= 0.0 && p->fuse_below >= 0 && p->jacobi_omega >= 0.0 &&
            p->tma_rows >= 0 && p->sell_rows >= 0 && p->sra_rounds >= 0 && p->sra_rounds <= 64 &&
-           p->wait_limit_ns >= 0 && p->cluster_below >= 0 && p->restrict_fuse_below >= 0;
+           p->wait_limit_ns >= 0 && p->cluster_below >= 0 && p->restrict_fuse_below >= 0 &&
+           (p->autotune == 0 || p->autotune == 1);
 }
 
 }  // namespace uaamg
@@ -112,6 +113,7 @@ void uaamg_default_params(uaamg_params* p) {
     p->fuse_below = 0;
     p->sra_rounds = 0;
     p->restrict_fuse_below = 0;
+    p->autotune = 0;
     p->cluster_below = 0;
     p->wait_limit_ns = 0;
 }
@@ -268,6 +270,21 @@ int uaamg_get_pass_of(const uaamg_handle* hh, int32_t l, int32_t* pass_of) {
     const Handle* h = reinterpret_cast<const Handle*>(hh);
     if (!h || !pass_of || l < 0 || l >= h->nlev - 1) return UAAMG_ERR_INVALID_ARG;
     return copy_out(h, pass_of, h->lev[l].pass_of, sizeof(int) * h->lev[l].n);
+}
+
+int uaamg_level_kernel(const uaamg_handle* hh, int32_t l, int32_t* path, int32_t* rows,
+                       double* us) {
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    if (!h || l < 0 || l >= h->nlev) return UAAMG_ERR_INVALID_ARG;
+    const Level& L = h->lev[l];
+    int pth = L.path;
+    if (pth < 0)  // by the size thresholds, as launch_rowblock decides
+        pth = L.sl_ptr ? 2 : (h->p.tma_rows > 0 && L.n >= h->p.tma_rows ? 1 : 0);
+    if (path) *path = pth;
+    if (rows) *rows = L.rb_rows;
+    if (us)
+        for (int c = 0; c < 6; c++) us[c] = L.tune_us[c];
+    return UAAMG_OK;
 }
 
 int uaamg_get_minv(const uaamg_handle* hh, int32_t l, double* minv) {

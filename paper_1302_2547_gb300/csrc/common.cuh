@@ -94,6 +94,12 @@ struct Level {
     int* members = nullptr;  // [n]
     int passes = 0;
     int rb_rows = kRowsPerBlock;  // rows per block of this level's row-block kernels
+    // SpMV kernel family of this level: -1 by the size thresholds (tma_rows, sell_rows),
+    // else chosen by the tuner: 0 row-block (rb_rows rows per block), 1 per-warp TMA,
+    // 2 sliced ELLPACK; tune_us holds the tuner's timings of its first sweep (row-block with
+    // 256, 128, 64, 32 rows per block, TMA, ELLPACK; -1 where not timed)
+    int path = -1;
+    float tune_us[6] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
     // sliced ELLPACK copy (levels with n >= sell_rows): slice offsets, row lengths, columns
     // and values in slice layout; null when not built
     int* sl_ptr = nullptr;
@@ -102,6 +108,7 @@ struct Level {
     double* sl_val64 = nullptr;
     float* sl_val32 = nullptr;
     int sl_ns = 0;
+    long long sl_padded = 0;  // entries of the slices, padding included
     // K-cycle workspace in the handle's precision
     void *rhs = nullptr, *out = nullptr, *w = nullptr, *s = nullptr;
     void *c1 = nullptr, *v1 = nullptr, *rt = nullptr, *c2 = nullptr, *v2 = nullptr;

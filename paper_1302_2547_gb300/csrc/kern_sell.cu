@@ -94,7 +94,25 @@ int build_sell(Handle* h, Level& L, bool mixed) {
     L.sl_val64 = sval64;
     L.sl_val32 = sval32;
     L.sl_ns = ns;
+    L.sl_padded = padded;
     return UAAMG_OK;
+}
+
+// Releases the level's sliced ELLPACK copy (stream-ordered).
+void drop_sell(Handle* h, Level& L) {
+    if (!L.sl_ptr) return;
+    dfree_one(h, L.sl_ptr, sizeof(int) * ((size_t)L.sl_ns + 1));
+    dfree_one(h, L.sl_len, sizeof(uint16_t) * (size_t)L.n);
+    dfree_one(h, L.sl_col, sizeof(int) * (size_t)L.sl_padded);
+    dfree_one(h, L.sl_val64, sizeof(double) * (size_t)L.sl_padded);
+    if (L.sl_val32) dfree_one(h, L.sl_val32, sizeof(float) * (size_t)L.sl_padded);
+    L.sl_ptr = nullptr;
+    L.sl_len = nullptr;
+    L.sl_col = nullptr;
+    L.sl_val64 = nullptr;
+    L.sl_val32 = nullptr;
+    L.sl_ns = 0;
+    L.sl_padded = 0;
 }
 
 template <typename T, int MODE, int ND>

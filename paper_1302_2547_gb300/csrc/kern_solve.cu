@@ -153,8 +153,10 @@ __global__ void __launch_bounds__(kThreads) k_rowblock(RBArgs<T> a) {
 
 template <typename T>
 int launch_rowblock(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
-    if (a.sptr) return launch_sell<T>(h, mode, ndots, a);  // sliced ELLPACK copy
-    if (h->p.tma_rows > 0 && a.n >= h->p.tma_rows)
+    // the level's kernel family: the tuner's choice, else the size thresholds
+    if (a.sptr && (a.path == 2 || a.path < 0))
+        return launch_sell<T>(h, mode, ndots, a);  // sliced ELLPACK copy
+    if (a.path == 1 || (a.path < 0 && h->p.tma_rows > 0 && a.n >= h->p.tma_rows))
         return launch_rowblock_tma<T>(h, mode, ndots, a);  // matrix stream via bulk copies
     const int grid = grid_for(a.n, a.rows);
     cudaStream_t st = h->work;

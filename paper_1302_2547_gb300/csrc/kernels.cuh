@@ -103,6 +103,7 @@ struct RBArgs {
     const T* sval;
     const uint16_t* slen;
     int nslices;
+    int path;  // kernel family chosen for the level (-1: by the size thresholds)
 };
 
 // Scalars of the fused modes, read once per thread at kernel start.
@@ -280,6 +281,9 @@ int launch_rowblock_tma(Handle* h, int mode, int ndots, const RBArgs<T>& a);
 template <typename T>
 int launch_sell(Handle* h, int mode, int ndots, const RBArgs<T>& a);
 int build_sell(Handle* h, Level& L, bool mixed);
+void drop_sell(Handle* h, Level& L);
+// per-level choice of the SpMV kernel family by timing the first sweep (tune.cu)
+int autotune_levels(Handle* h);
 
 template <typename T>
 int launch_restrict(Handle* h, int nc, const int* aggptr, const int* members, const T* s,

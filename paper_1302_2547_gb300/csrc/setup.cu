@@ -397,6 +397,8 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
             }
         }
     }
+    // per-level kernel choice by timing (after the workspace exists)
+    if (st == UAAMG_OK && h->p.autotune) st = autotune_levels(h);
 done:
     dfree_temps(h);
     if (hb) cudaFreeHost(hb);

@@ -74,9 +74,16 @@ static double class_bytes(const Handle* h, int cls) {
     return 0.0;
 }
 
+// Whether the level's SpMV-based kernels run as the per-warp TMA pipelines.
+static bool on_tma(const Handle* h, const Level& L) {
+    if (L.path >= 0) return L.path == 1;
+    return !L.sl_ptr && h->p.tma_rows > 0 && L.n >= h->p.tma_rows;
+}
+
 template <typename T>
 static RBArgs<T> rb_args(Handle* h, const Level& L) {
     RBArgs<T> a{};
+    a.path = L.path;
     a.n = L.n;
     a.nnz = L.nnz;
     a.rows = L.rb_rows;
@@ -144,7 +151,7 @@ static int apply_B(Handle* h, int l, const T* in, T* out, const RtFuse<T>* rf = 
         // levels of the row-block kernels with one pre-sweep: the sweep and the restriction
         // in one launch (the large levels keep the bandwidth-tuned sweep and restrict apart)
         const bool fused = pre == 1 && !a.sptr && L.n <= h->p.restrict_fuse_below &&
-                           !(h->p.tma_rows > 0 && L.n >= h->p.tma_rows);
+                           !on_tma(h, L);
         int ps = prof_begin(h, UAAMG_KCLASS_SMOOTH0, l);
         if (fused) st = launch_pre1_restrict<T>(h, mode, a, L.nc, L.aggptr, L.members, rc);
         else st = launch_rowblock<T>(h, mode, 0, a);
@@ -176,8 +183,7 @@ static int apply_B(Handle* h, int l, const T* in, T* out, const RtFuse<T>* rf = 
     }
     // on a large level the fused form costs more in the sweep (registers, two gathers per
     // coarse value) than one combine launch on the child saves
-    const bool defer = post >= 1 && can_defer(h, l + 1) &&
-                       !(h->p.tma_rows > 0 && L.n >= h->p.tma_rows);
+    const bool defer = post >= 1 && can_defer(h, l + 1) && !on_tma(h, L);
     if ((st = apply_K<T>(h, l + 1, rc, ec, defer))) return st;
     {
         RBArgs<T> a = rb_args<T>(h, L);
@@ -286,6 +292,7 @@ static int outer_iteration(Handle* h, bool to_host) {
     if ((st = launch_outer_p<T>(h, n, z, h->p_, h->osc))) return st;
     {
         RBArgs<double> a{};
+        a.path = L0.path;
         a.n = n;
         a.nnz = L0.nnz;
         a.rows = L0.rb_rows;
@@ -456,6 +463,7 @@ static int iterate_once(Handle* h) {
 static int true_residual(Handle* h) {
     Level& L0 = h->lev[0];
     RBArgs<double> a{};
+    a.path = L0.path;
     a.n = L0.n;
     a.nnz = L0.nnz;
     a.rows = L0.rb_rows;

@@ -1,0 +1,68 @@
+"""The kernel autotuner (autotune = 1): every level of at least 32768 unknowns is timed on
+the row-block kernel (256/128/64/32 rows per block), the per-warp TMA kernel and the sliced
+ELLPACK kernel, and keeps the fastest.  Whatever it chooses, the operators and solves meet
+the same bars against the oracle as the threshold-chosen kernels (the candidates differ
+only in how a row's sum is split between lanes)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotuned_levels_meet_the_oracle_bars(oracle, inputs, precision):
+    from paper_1302_2547_gb300 import _lib as U
+    from paper_1302_2547_gb300 import build as B
+
+    B.build()
+    I = inputs
+    prec = U.UAAMG_FP64 if precision == "fp64" else U.UAAMG_MIXED
+    cases = [(I.grid3d(48, sigma=0.25, seed=4), dict(max_agg_size=4, agg_repeat=2,
+                                                     kcycle_ratio=5.0, min_coarsening=1.5)),
+             (I.rgg(120000, 8.0, seed=6), dict(max_agg_size=0, kcycle_ratio=3.0,
+                                               min_coarsening=1.5))]
+    keys = ("coarse_size", "max_levels", "max_agg_size", "pass_mode", "seed", "pre", "post",
+            "kcycle_inner", "kcycle_tau", "max_iter", "agg_repeat", "kcycle_ratio",
+            "min_coarsening", "jacobi_omega")
+    for A, kw in cases:
+        p = U.uaamg_default_params(precision=prec, autotune=1, **kw)
+        h = U.uaamg_setup(A.rowptr, A.col, A.val, p)
+        H = oracle.Hierarchy(A.rowptr, A.col, A.val,
+                             oracle.Params(**{k: getattr(p, k) for k in keys}))
+        try:
+            tuned = 0
+            for l in range(U.uaamg_num_levels(h) - 1):
+                n = U.uaamg_level_info(h, l)[0]
+                k = U.uaamg_level_kernel(h, l)
+                assert k["path"] in (0, 1, 2)
+                if n >= 32768:
+                    tuned += 1
+                    us = k["tune_us"]
+                    assert all(u > 0 for u in us[:5]), us  # row-block x4 and TMA timed
+                    chosen = {0: us[[256, 128, 64, 32].index(k["rows"])] if k["path"] == 0
+                              else None, 1: us[4], 2: us[5]}[k["path"]]
+                    assert chosen == min(u for u in us if u > 0)
+                else:
+                    assert k["tune_us"] == [-1.0] * 6
+            assert tuned >= 1
+            r = np.random.default_rng(3).standard_normal(A.n)
+            g, o = U.uaamg_apply_B(h, 0, r), H.apply_B(0, r)
+            tol = 1e-10 if prec == U.UAAMG_FP64 else 2e-5
+            assert np.linalg.norm(g - o) <= tol * np.linalg.norm(o)
+            assert np.max(np.abs(g - o)) <= tol * np.max(np.abs(o))
+            b = I.rhs_uniform(A.n, 11)
+            x = np.zeros(A.n)
+            st, it, rr = U.uaamg_solve(h, b, x, 1e-8)
+            xo, ito, _, sto, _ = H.solve(b, 1e-8)
+            Asp = sp.csr_matrix((A.val, A.col, A.rowptr))
+            bn = np.linalg.norm(b)
+            assert st == 0 and sto == 0
+            assert np.linalg.norm(b - Asp @ x) <= 1e-8 * bn * 1.0001
+            assert np.linalg.norm(Asp @ (x - xo)) <= 2.0001e-8 * bn
+            if prec == U.UAAMG_FP64:
+                assert abs(it - ito) <= 1
+            else:
+                assert it <= ito + 5
+        finally:
+            U.uaamg_free(h)
