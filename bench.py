@@ -669,6 +669,45 @@ def measure_fp64():
             "method": "CUDA events over FMA recurrences on a full grid of resident blocks"}
 
 
+def run_autotune_report():
+    """One setup of the headline system with the kernel autotuner on: the kernel family it
+    keeps per level and its timings of one visit's kernels per candidate (the headline runs
+    the size thresholds; this measures Section 4.4's ELLPACK-versus-CSR question on it)."""
+    import torch
+
+    from paper_1302_2547_gb300 import _lib as U
+
+    A, b = workload()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rp, cc, vv = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.col, A.val))
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    out = {}
+    for name, prec in (("mixed", U.UAAMG_MIXED), ("fp64", U.UAAMG_FP64)):
+        p = U.uaamg_default_params(precision=prec, autotune=1, **BENCH_PARAMS)
+        h = U.uaamg_setup(rp, cc, vv, p)
+        try:
+            st, it, rr = U.uaamg_solve(h, bd, xd, TOL)
+            lv = []
+            for l in range(U.uaamg_num_levels(h) - 1):
+                k = U.uaamg_level_kernel(h, l)
+                if k["tune_us"][0] <= 0:
+                    continue
+                lv.append({"level": l, "n": U.uaamg_level_info(h, l)[0],
+                           "kept": ["row-block", "TMA", "ELLPACK"][k["path"]],
+                           "rows_per_block": k["rows"],
+                           "visit_us": dict(zip(["rb256", "rb128", "rb64", "rb32", "tma",
+                                                 "ellpack"], k["tune_us"]))})
+            out[name] = {"levels": lv, "solve_ms_tuned": round(U.uaamg_get_stats(h)["solve_ms"], 3),
+                         "iterations": it}
+        finally:
+            U.uaamg_free(h)
+    out["note"] = ("visit_us: the first sweep, the prolongation sweep and the SpMV with two "
+                   "inner products of one visit (level 0: also the FP64 outer SpMV), back to "
+                   "back, per candidate kernel family")
+    return out
+
+
 def run_setup_rooflines(steps=3, warmup=1):
     """Live rooflines of the two setup kernels of level 0 of the headline system: the
     aggregation kernel (every pass: two sweeps over the adjacency of its vertices) and the
@@ -1143,6 +1182,10 @@ def main():
             except Exception as e:  # reported, not hidden: the main line still stands
                 out["sra"] = {"error": f"{type(e).__name__}: {e}"}
         if world == 1:
+            try:
+                out["autotune"] = run_autotune_report()
+            except Exception as e:  # reported, not hidden: the main line still stands
+                out["autotune"] = {"error": f"{type(e).__name__}: {e}"}
             try:
                 out["setup_roofline"] = run_setup_rooflines()
             except Exception as e:  # reported, not hidden: the main line still stands

@@ -120,13 +120,15 @@ typedef struct uaamg_params {
                                     restriction in one launch, a warp per aggregate; 0 = never
                                     (default: on GB300 the two launches are faster except on
                                     hierarchies of a few thousand unknowns) */
-    int32_t autotune;     /* 1: at the end of setup, time each level's first sweep (levels of
-                             at least 32768 unknowns) with the row-block kernel at 256, 128, 64
-                             and 32 rows per block, the per-warp TMA kernel and the sliced
-                             ELLPACK kernel, and keep the fastest for the level's SpMV-based
-                             kernels (remembered per level shape for the process); 0 (default):
-                             the size thresholds tma_rows and sell_rows decide.  Changes the
-                             rounding of row sums only (the lanes a row is split into). */
+    int32_t autotune;     /* 1: at the end of setup, time the SpMV-based kernels of a visit of
+                             each level of at least 32768 unknowns (first sweep, prolongation
+                             sweep, SpMV with two inner products; on level 0 also the FP64
+                             outer SpMV) with the row-block kernel at 256, 128, 64 and 32 rows
+                             per block, the per-warp TMA kernel and the sliced ELLPACK kernel,
+                             and keep the fastest for the level (remembered per level shape for
+                             the process); 0 (default): the size thresholds tma_rows and
+                             sell_rows decide.  Changes the rounding of row sums only (the
+                             lanes a row is split into). */
     int32_t cluster_below; /* coarse levels with at most this many unknowns run their K-cycle
                               in one launch on one thread-block cluster (pre = post = 1 only;
                               8 or 16 blocks that synchronise by cluster barriers and exchange
@@ -241,9 +243,9 @@ int uaamg_get_level_csr(const uaamg_handle* h, int32_t l, int32_t* rowptr, int32
 int uaamg_get_priorities(const uaamg_handle* h, int32_t l, uint64_t* P);
 int uaamg_get_pass_of(const uaamg_handle* h, int32_t l, int32_t* pass_of);
 /* The kernel family level l's SpMV-based kernels run (*path: 0 row-block with *rows rows
- * per block, 1 per-warp TMA, 2 sliced ELLPACK) and the autotuner's first-sweep timings in
- * microseconds (us[6]: row-block 256, 128, 64, 32, TMA, ELLPACK; -1 where not timed, all -1
- * when the level was not tuned). */
+ * per block, 1 per-warp TMA, 2 sliced ELLPACK) and the autotuner's timings of one visit's
+ * kernels in microseconds (us[6]: row-block 256, 128, 64, 32, TMA, ELLPACK; -1 where not
+ * timed, all -1 when the level was not tuned). */
 int uaamg_level_kernel(const uaamg_handle* h, int32_t l, int32_t* path, int32_t* rows,
                        double* us);
 /* Host copy of the FP64 l1-Jacobi diagonal Minv_i = 1 / (a_ii + sum_{j!=i} |a_ij|). */
