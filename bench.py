@@ -1098,6 +1098,8 @@ def main():
                     help="do not time subgraph reshaping (Algorithm 3) on the workload")
     ap.add_argument("--sra-only", action="store_true",
                     help="print only the subgraph-reshaping measurement as one JSON line")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the headline mixed-precision steps (for profilers)")
     ap.add_argument("--skip-c4", action="store_true",
                     help="do not run the batched workload (512 systems x 16 right-hand sides)")
     ap.add_argument("--c4-only", action="store_true",
@@ -1120,6 +1122,10 @@ def main():
     ap.add_argument("--sell-rows", type=int, default=None,
                     help="row threshold of the sliced ELLPACK level copies (0 = off)")
     args = ap.parse_args()
+    if args.headline_only:
+        for k in ("skip_e2e", "skip_cpu_baseline", "skip_plain", "skip_batched", "skip_serving",
+                  "skip_sra", "skip_c4", "skip_rgg", "skip_poisson64", "skip_extras"):
+            setattr(args, k, True)
     global EAGER, TMA_ROWS, FUSE_BELOW, SELL_ROWS, CLUSTER_BELOW, AUTOTUNE
     EAGER = args.eager
     TMA_ROWS = args.tma_rows
@@ -1181,7 +1187,7 @@ def main():
                 out["sra"] = run_sra()
             except Exception as e:  # reported, not hidden: the main line still stands
                 out["sra"] = {"error": f"{type(e).__name__}: {e}"}
-        if world == 1:
+        if world == 1 and not getattr(args, "skip_extras", False):
             try:
                 out["autotune"] = run_autotune_report()
             except Exception as e:  # reported, not hidden: the main line still stands
