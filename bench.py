@@ -67,11 +67,15 @@ NCU_SOURCES = {
     "coarse": ("kern_setup.cu", "kernels.cuh", "common.cuh"),
 }
 NCU_TRAFFIC = {
-    # level 0 of the 128^3 system, ncu --set full
-    # k_rowwarp_tma<float, RB_PRE1>: 141,838,336 + 7,883,520 bytes
-    ("smooth0", "0defb33c3b3547d4"): 149721856,
-    # k_rowwarp_tma<double, RB_SPMV, 2 dots>: 216,973,312 + 12,700,160 bytes
-    ("spmv64", "0defb33c3b3547d4"): 229673472,
+    # level 0 of the 128^3 system, ncu --set full (one capture per launch)
+    # k_rowwarp_tma<float, RB_PRE1>: 141,836,544 + 8,271,104 bytes
+    ("smooth0", "118ce82ac812d088"): 150107648,
+    # k_rowwarp_tma<double, RB_SPMV, 2 dots>: 216,965,888 + 12,919,296 bytes
+    ("spmv64", "118ce82ac812d088"): 229885184,
+    # k_paa_sr<1> on level 0 (one launch, every pass): 1.88395 GB + 560,823,040 bytes
+    ("paa", "b55b623873278b85"): 2444773040,
+    # k_coarse_build on level 0 (first stage): 266,696,000 + 109,914,624 bytes
+    ("coarse", "b55b623873278b85"): 376610624,
 }
 
 
@@ -739,7 +743,8 @@ def run_setup_rooflines(steps=3, warmup=1):
         out[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
                      "algorithmic_bytes_per_launch": by, "avg_launch_us": round(avg * 1e6, 1),
-                     "launches_timed": launches, "traffic": None,
+                     "launches_timed": launches,
+                     "traffic": NCU_TRAFFIC.get((name, _src_hash(name))),
                      "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
     out["paa"]["kernel"] = "the single-round aggregation passes of level 0 (one launch)"
     out["coarse"]["kernel"] = "coarse-operator assembly of level 0 (first stage)"

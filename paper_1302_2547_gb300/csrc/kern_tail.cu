@@ -312,9 +312,42 @@ __device__ __forceinline__ void cluster_sum(double (&v)[ND], double (*part)[3], 
     for (int k = 0; k < ND; k++) v[k] = tot[k];
 }
 
-template <typename T, typename G>
-__device__ __forceinline__ T cl_row(const TailLevel& L, int i, G g) {
-    return tail_row<T>(L, i, g);
+// Every row of level L, 1 to 8 lanes per row by its mean row length: the lanes of a row take
+// its entries in turn
+// (each lane's own entries in stored order, eight loads in flight), combine their sums by a
+// fixed shuffle tree, and the row's first lane calls epi(i, sum).  The loop is uniform over
+// each warp (whole warps of rows), so the shuffles see every lane.  gw / nw: this warp's
+// index and the warps of the cluster.
+template <typename T, typename G, typename E>
+__device__ __forceinline__ void cl_rows(const TailLevel& L, int gw, int nw, G g, E epi) {
+    // a few entries per lane, so that one batch of gathers covers a row
+    const int avg = L.rowptr[L.n] / (L.n > 0 ? L.n : 1);
+    const int lpr = avg < 6 ? 1 : avg < 12 ? 2 : avg < 24 ? 4 : 8;
+    const int lane = threadIdx.x & 31, sub = lane & (lpr - 1);
+    const int rpw = 32 / lpr;
+    const T* val = (const T*)L.val;
+    for (int base = gw * rpw; base < L.n; base += nw * rpw) {
+        const int i = base + lane / lpr;
+        T acc = T(0);
+        if (i < L.n) {
+            const int k1 = L.rowptr[i + 1];
+            for (int k = L.rowptr[i] + sub; k < k1; k += kTailBatch * lpr) {
+                T xg[kTailBatch], vv[kTailBatch];
+#pragma unroll
+                for (int u = 0; u < kTailBatch; u++) {
+                    const int kk = k + u * lpr;
+                    const bool in = kk < k1;
+                    xg[u] = in ? g(L.col[kk]) : T(0);
+                    vv[u] = in ? val[kk] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < kTailBatch; u++)
+                    if (k + u * lpr < k1) acc = fma_rn(vv[u], xg[u], acc);
+            }
+        }
+        for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, lpr);
+        if (i < L.n && sub == 0) epi(i, acc);
+    }
 }
 
 template <typename T>
@@ -331,6 +364,7 @@ k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double 
     int slot = 0;
     const int G = (int)cl.num_blocks() * kClusterThreads;
     const int g0 = (int)cl.block_rank() * kClusterThreads + threadIdx.x;
+    const int nw = G >> 5, gw = g0 >> 5;  // warps of the cluster, this warp's index
     if (threadIdx.x == 0) {
         st[0] = TailFrame{0, m0, 0, lv[m0].rhs, lv[m0].out, 0.0, 0.0, 0.0};
         sp = 1;
@@ -367,13 +401,14 @@ k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double 
                 next_phase = 1;
             } else if (f.phase == 1) {  // v1 = A c1; rho1, alpha1; rho~
                 double d[3] = {0.0, 0.0, 0.0};
-                for (int i = g0; i < L.n; i += G) {
-                    const T acc = cl_row<T>(L, i, [&](int j) { return ldg_cg(c1 + j); });
-                    v1[i] = acc;
-                    const double xi = (double)ldg_cg(c1 + i);
-                    d[0] = fma(xi, (double)acc, d[0]);
-                    d[1] = fma(xi, (double)ldg_cg(in + i), d[1]);
-                }
+                cl_rows<T>(
+                    L, gw, nw, [&](int j) { return ldg_cg(c1 + j); },
+                    [&](int i, T acc) {
+                        v1[i] = acc;
+                        const double xi = (double)ldg_cg(c1 + i);
+                        d[0] = fma(xi, (double)acc, d[0]);
+                        d[1] = fma(xi, (double)ldg_cg(in + i), d[1]);
+                    });
                 cluster_sum<3>(d, part, slot);
                 slot ^= 1;
                 // the step's scalars in one thread (FP64 divisions are costly on GB300's
@@ -413,14 +448,15 @@ k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double 
                 }
             } else if (f.phase == 2) {  // v2 = A c2; beta, gamma, alpha2
                 double d[3] = {0.0, 0.0, 0.0};
-                for (int i = g0; i < L.n; i += G) {
-                    const T acc = cl_row<T>(L, i, [&](int j) { return ldg_cg(c2 + j); });
-                    v2[i] = acc;
-                    const double xi = (double)ldg_cg(c2 + i);
-                    d[0] = fma(xi, (double)acc, d[0]);
-                    d[1] = fma(xi, (double)ldg_cg(v1 + i), d[1]);
-                    d[2] = fma(xi, (double)ldg_cg(rt + i), d[2]);
-                }
+                cl_rows<T>(
+                    L, gw, nw, [&](int j) { return ldg_cg(c2 + j); },
+                    [&](int i, T acc) {
+                        v2[i] = acc;
+                        const double xi = (double)ldg_cg(c2 + i);
+                        d[0] = fma(xi, (double)acc, d[0]);
+                        d[1] = fma(xi, (double)ldg_cg(v1 + i), d[1]);
+                        d[2] = fma(xi, (double)ldg_cg(rt + i), d[2]);
+                    });
                 cluster_sum<3>(d, part, slot);
                 slot ^= 1;
                 if (threadIdx.x == 0) {  // only thread 0 keeps the frame's scalars
@@ -449,12 +485,12 @@ k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double 
             T* rc = (T*)C.rhs;
             T* ec = (T*)C.out;
             if (f.phase == 0) {
-                for (int i = g0; i < L.n; i += G) {
-                    const T acc =
-                        cl_row<T>(L, i, [&](int j) { return mul_rn(minv[j], ldg_cg(in + j)); });
-                    x[i] = mul_rn(minv[i], ldg_cg(in + i));
-                    s[i] = sub_rn(ldg_cg(in + i), acc);
-                }
+                cl_rows<T>(
+                    L, gw, nw, [&](int j) { return mul_rn(minv[j], ldg_cg(in + j)); },
+                    [&](int i, T acc) {
+                        x[i] = mul_rn(minv[i], ldg_cg(in + i));
+                        s[i] = sub_rn(ldg_cg(in + i), acc);
+                    });
                 cl.sync();  // every block's s before the restriction
                 for (int I = g0; I < C.n; I += G) {
                     const int q1 = L.aggptr[I + 1];
@@ -474,13 +510,13 @@ k_tail_cluster(const TailLevel* lv, int m0, int nlev, const double* inv, double 
                 push = 1;
                 next_phase = 1;
             } else {
-                for (int i = g0; i < L.n; i += G) {
-                    const T acc = cl_row<T>(L, i, [&](int j) {
-                        return add_rn(ldg_cg(x + j), ldg_cg(ec + L.agg[j]));
+                cl_rows<T>(
+                    L, gw, nw,
+                    [&](int j) { return add_rn(ldg_cg(x + j), ldg_cg(ec + L.agg[j])); },
+                    [&](int i, T acc) {
+                        const T xi = add_rn(ldg_cg(x + i), ldg_cg(ec + L.agg[i]));
+                        out[i] = add_rn(xi, mul_rn(minv[i], sub_rn(ldg_cg(in + i), acc)));
                     });
-                    const T xi = add_rn(ldg_cg(x + i), ldg_cg(ec + L.agg[i]));
-                    out[i] = add_rn(xi, mul_rn(minv[i], sub_rn(ldg_cg(in + i), acc)));
-                }
                 pop = 1;
             }
         }
