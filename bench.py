@@ -390,6 +390,8 @@ def run_gpu(args, rank, world):
                        "p99": round(float(np.percentile(lat, 99)), 3)},
         "iterations": int(np.median(its)), "relres_host_fp64": relres_host,
         "levels": stats["levels"], "coarsest_n": stats["coarsest_n"],
+        "cluster_tail": {"first_level": stats["tail_level"], "blocks": stats["tail_blocks"],
+                         "graph_nodes_per_iteration": stats["graph_nodes"]},
         "level_kernels": [{"level": k["level"], "n": k["n"],
                            "kernel": ["row-block", "TMA", "ELLPACK"][k["path"]],
                            "rows_per_block": k["rows"],

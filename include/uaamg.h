@@ -129,11 +129,17 @@ typedef struct uaamg_params {
                              the process); 0 (default): the size thresholds tma_rows and
                              sell_rows decide.  Changes the rounding of row sums only (the
                              lanes a row is split into). */
-    int32_t cluster_below; /* coarse levels with at most this many unknowns run their K-cycle
-                              in one launch on one thread-block cluster (pre = post = 1 only;
-                              8 or 16 blocks that synchronise by cluster barriers and exchange
-                              inner products through distributed shared memory); 0 = off.
-                              Takes precedence over fuse_below. */
+    int32_t cluster_below; /* coarse levels with at most this many unknowns (and at most 65536)
+                              run their K-cycle in one launch on one thread-block cluster
+                              (pre = post = 1 only): 16 blocks (8 where the device does not
+                              run 16) that hold the levels' vectors and matrices in shared
+                              memory, replicate the vectors other blocks gather through
+                              distributed shared memory and synchronise by cluster barriers.
+                              The tail starts at the first such level whose data fit in the
+                              cluster's shared memory, else lower.  Default 8192; 0 = off.
+                              Takes precedence over fuse_below.  Changes the rounding of the
+                              K-cycle's inner products (FP32 pairs in mixed precision) and of
+                              row sums split across lanes. */
     int64_t wait_limit_ns; /* limit of every bounded device-side wait of this handle: a grid
                               barrier of a cooperative kernel, a wait for a bulk copy into
                               shared memory (measured in SM clock cycles, about 2 per ns).
@@ -267,6 +273,8 @@ typedef struct uaamg_stats {
     double opc;           /* operator complexity sum_l nnz_l / nnz_0 */
     double grid_complexity;
     uint64_t device_bytes; /* device memory the handle holds now (hierarchy and workspace) */
+    int32_t tail_level;    /* first level of the fused small-level K-cycle kernel, 0 = none */
+    int32_t tail_blocks;   /* its thread blocks: the cluster size, 1 for the one-block kernel */
 } uaamg_stats;
 int uaamg_get_stats(const uaamg_handle* h, uaamg_stats* s);
 

@@ -58,7 +58,8 @@ class uaamg_params(C.Structure):
 class uaamg_stats(C.Structure):
     _fields_ = [("setup_ms", C.c_double), ("solve_ms", C.c_double), ("launches", C.c_int64),
                 ("graph_nodes", C.c_int64), ("opc", C.c_double),
-                ("grid_complexity", C.c_double), ("device_bytes", C.c_uint64)]
+                ("grid_complexity", C.c_double), ("device_bytes", C.c_uint64),
+                ("tail_level", C.c_int32), ("tail_blocks", C.c_int32)]
 
 
 class uaamg_answer(C.Structure):

@@ -114,7 +114,7 @@ void uaamg_default_params(uaamg_params* p) {
     p->sra_rounds = 0;
     p->restrict_fuse_below = 0;
     p->autotune = 0;
-    p->cluster_below = 0;
+    p->cluster_below = 8192;
     p->wait_limit_ns = 0;
 }
 
@@ -334,6 +334,8 @@ int uaamg_get_stats(const uaamg_handle* hh, uaamg_stats* s) {
     s->opc = z / (double)h->lev[0].nnz;
     s->grid_complexity = nn / (double)h->lev[0].n;
     s->device_bytes = (uint64_t)h->bytes;
+    s->tail_level = h->tail_level;
+    s->tail_blocks = h->tail_level > 0 ? (h->tail_cluster ? h->tail_cl : 1) : 0;
     return UAAMG_OK;
 }
 

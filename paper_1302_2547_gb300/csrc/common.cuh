@@ -157,6 +157,12 @@ struct Handle {
     int tail_level = 0;
     bool tail_cluster = false;  // the tail runs on a thread-block cluster (else one block)
     TailLevel* tail_dev = nullptr;
+    // cluster tail: per-block regions of packed level data (tail_stride bytes apart, the
+    // first tail_copy bytes of each staged at byte tail_vb of the block's shared memory),
+    // blocks per cluster and dynamic shared memory per block
+    void* tail_blob = nullptr;
+    long long tail_stride = 0;
+    int tail_copy = 0, tail_vb = 0, tail_cl = 0, tail_smem = 0;
     // uaamg_solve_many workspace (sized for multi_R columns) and its iteration graph
     int multi_R = 0;
     MultiLevel mlev[kMaxLevels];

@@ -310,6 +310,9 @@ int launch_prolong(Handle* h, int n, const T* x, const int* agg, const T* e, T* 
 // fused K-cycle of the levels m0 .. L-1 (kern_tail.cu)
 template <typename T>
 int launch_tail(Handle* h, int m0);
+// Packs the cluster tail's per-block regions, starting at level m_first or, where those
+// levels do not fit in shared memory, lower; sets h->tail_level (left 0 when none fits).
+int tail_cluster_prepare(Handle* h, int m_first);
 
 // R right-hand sides at once (kern_multi.cu)
 template <typename T>

@@ -349,51 +349,57 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
         }
         if (cudaMallocHost(&h->osc_host, sizeof(OuterScalars)) != cudaSuccess) st = UAAMG_ERR_OOM;
     }
-    {  // levels small enough for the fused K-cycle kernel (one pre- and post-sweep only)
-        int m0 = 0;
-        const int below = std::max(h->p.fuse_below, h->p.cluster_below);
-        if (h->p.pre == 1 && h->p.post == 1)
-            for (int l = 1; l < h->nlev - 1; l++)
-                if (h->lev[l].n <= below) {
-                    m0 = l;
-                    break;
+    {  // levels small enough for a fused K-cycle kernel (one pre- and post-sweep only): the
+        // cluster kernel where its levels fit in the cluster's shared memory, else one block
+        auto first_below = [&](int below) {
+            if (h->p.pre == 1 && h->p.post == 1)
+                for (int l = 1; l < h->nlev - 1; l++)
+                    if (h->lev[l].n <= below) return l;
+            return 0;
+        };
+        if (st == UAAMG_OK && h->p.cluster_below > 0) {
+            const int m = first_below(h->p.cluster_below);
+            if (m > 0) st = tail_cluster_prepare(h, m);
+        }
+        if (st == UAAMG_OK && h->tail_level == 0) {
+            const int m0 = first_below(h->p.fuse_below);
+            h->tail_cluster = false;
+            if (m0 > 0) {
+                std::vector<TailLevel> tl(h->nlev);
+                for (int l = 0; l < h->nlev; l++) {
+                    const Level& L = h->lev[l];
+                    TailLevel& t = tl[l];
+                    memset(&t, 0, sizeof(t));
+                    t.n = L.n;
+                    int inner = h->p.kcycle_inner;
+                    if (l >= 1 && inner == 2 && h->p.kcycle_ratio > 0.0 &&
+                        (double)h->lev[l - 1].n < h->p.kcycle_ratio * (double)L.n)
+                        inner = 1;
+                    t.inner = inner;
+                    t.rowptr = L.rowptr;
+                    t.col = L.col;
+                    t.agg = L.agg;
+                    t.aggptr = L.aggptr;
+                    t.members = L.members;
+                    t.val = mixed ? (const void*)L.val32 : (const void*)L.val64;
+                    t.minv = mixed ? (const void*)L.minv32 : (const void*)L.minv64;
+                    t.rhs = L.rhs;
+                    t.out = L.out;
+                    t.w = L.w;
+                    t.s = L.s;
+                    t.c1 = L.c1;
+                    t.v1 = L.v1;
+                    t.rt = L.rt;
+                    t.c2 = L.c2;
+                    t.v2 = L.v2;
                 }
-        h->tail_cluster = m0 > 0 && h->lev[m0].n <= h->p.cluster_below;
-        if (m0 > 0 && st == UAAMG_OK) {
-            std::vector<TailLevel> tl(h->nlev);
-            for (int l = 0; l < h->nlev; l++) {
-                const Level& L = h->lev[l];
-                TailLevel& t = tl[l];
-                memset(&t, 0, sizeof(t));
-                t.n = L.n;
-                int inner = h->p.kcycle_inner;
-                if (l >= 1 && inner == 2 && h->p.kcycle_ratio > 0.0 &&
-                    (double)h->lev[l - 1].n < h->p.kcycle_ratio * (double)L.n)
-                    inner = 1;
-                t.inner = inner;
-                t.rowptr = L.rowptr;
-                t.col = L.col;
-                t.agg = L.agg;
-                t.aggptr = L.aggptr;
-                t.members = L.members;
-                t.val = mixed ? (const void*)L.val32 : (const void*)L.val64;
-                t.minv = mixed ? (const void*)L.minv32 : (const void*)L.minv64;
-                t.rhs = L.rhs;
-                t.out = L.out;
-                t.w = L.w;
-                t.s = L.s;
-                t.c1 = L.c1;
-                t.v1 = L.v1;
-                t.rt = L.rt;
-                t.c2 = L.c2;
-                t.v2 = L.v2;
-            }
-            h->tail_dev = dalloc<TailLevel>(h, h->nlev, &st);
-            if (st == UAAMG_OK) {
-                st = check_cuda(cudaMemcpyAsync(h->tail_dev, tl.data(), sizeof(TailLevel) * h->nlev,
-                                                cudaMemcpyHostToDevice, h->work));
-                if (st == UAAMG_OK) st = check_cuda(cudaStreamSynchronize(h->work));
-                h->tail_level = m0;
+                h->tail_dev = dalloc<TailLevel>(h, h->nlev, &st);
+                if (st == UAAMG_OK) {
+                    st = check_cuda(cudaMemcpyAsync(h->tail_dev, tl.data(), sizeof(TailLevel) * h->nlev,
+                                                    cudaMemcpyHostToDevice, h->work));
+                    if (st == UAAMG_OK) st = check_cuda(cudaStreamSynchronize(h->work));
+                    h->tail_level = m0;
+                }
             }
         }
     }

@@ -164,10 +164,16 @@ def test_kcycle_operator(oracle, precision, tail):
     """K_1 and B_0 against the oracle with levels from 1 down run by the one-block fused
     cycle, by the thread-block-cluster cycle, or launch by launch."""
     A = I.grid2d(60)
-    kw = {"block": {"fuse_below": 8192}, "cluster": {"cluster_below": 8192}, "off": {}}[tail]
+    kw = {"block": {"fuse_below": 8192, "cluster_below": 0}, "cluster": {"cluster_below": 8192},
+          "off": {"cluster_below": 0}}[tail]
     h, H, _ = both(A, oracle, precision=precision, **kw)
     try:
         assert U.uaamg_num_levels(h) >= 3
+        s = U.uaamg_get_stats(h)
+        assert s["tail_level"] == (0 if tail == "off" else 1), s
+        assert s["tail_blocks"] == {"block": 1, "cluster": s["tail_blocks"], "off": 0}[tail]
+        if tail == "cluster":
+            assert s["tail_blocks"] in (8, 16), s
         rho = np.random.default_rng(1).standard_normal(H.n(1))
         g, o = U.uaamg_apply_K(h, 1, rho), H.apply_K(1, rho)
         tol = 1e-10 if precision == U.UAAMG_FP64 else 2e-5
