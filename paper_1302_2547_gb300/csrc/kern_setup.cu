@@ -140,6 +140,8 @@ struct PaaArgs {
     int* slots;
     int nslots;
     Ctrl* ctrl;
+    int handoff;  // grid kernel: hand the passes to the cluster kernel once a pass has at most
+                  // this many candidates (0: never)
 };
 
 __device__ __forceinline__ uint8_t ld_state(const uint8_t* p) {
@@ -198,27 +200,54 @@ constexpr int kPaaThreads = 1024;  // large blocks: fewer arrivals at each grid 
 
 constexpr int kPaaBatch = 4;  // neighbour steps whose loads are issued together
 
-template <int G>
-__global__ void __launch_bounds__(kPaaThreads, 2) k_paa_sr(PaaArgs a) {
+// Once a pass has few candidates, a pass is a chain of dependent L2 round trips plus two
+// barriers, and a barrier over the whole grid costs several times one over a cluster of
+// 16 SMs.  So the cooperative grid kernel (CL = false) hands the remaining passes to the
+// same kernel launched as one thread-block cluster (CL = true), which synchronises with
+// cluster barriers (release / acquire at cluster scope order the global-memory state).
+// The hand-off leaves ctrl->npasses = -(next pass + 1); the cluster kernel resumes there,
+// or returns at once when the grid kernel finished (npasses >= 0) or failed.
+__device__ __forceinline__ void paa_cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+template <bool CL>
+__device__ __forceinline__ bool paa_barrier(Ctrl* ctrl) {
+    if constexpr (CL) {
+        paa_cluster_barrier();
+        return true;
+    } else {
+        return grid_barrier(ctrl);
+    }
+}
+
+template <int G, bool CL>
+__global__ void __launch_bounds__(kPaaThreads, CL ? 1 : 2) k_paa_sr(PaaArgs a) {
     const int n = a.n;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
     // cp[v] = P_v while v is a candidate, 0 once aggregated: one load answers both "is it a
     // candidate" and "with what priority"
     unsigned long long* cp = reinterpret_cast<unsigned long long*>(a.cprio);
-    for (int v = tid; v < n; v += nthreads) {
-        cp[v] = a.prio[v];
-        a.root_of[v] = -1;
-        a.pass_of[v] = -1;
+    int prev_cnt = n, pass = 0;
+    if constexpr (CL) {  // resume where the grid kernel handed off (uniform over the cluster)
+        const int np = *(volatile const int*)&a.ctrl->npasses;
+        if (np >= 0 || *(volatile const int*)&a.ctrl->err) return;
+        pass = -np - 1;
+        prev_cnt = *(volatile const int*)&a.slots[pass - 1];
+    } else {
+        for (int v = tid; v < n; v += nthreads) {
+            cp[v] = a.prio[v];
+            a.root_of[v] = -1;
+            a.pass_of[v] = -1;
+        }
+        if (!grid_barrier(a.ctrl)) return;
     }
-    if (!grid_barrier(a.ctrl)) return;
     const int lane = threadIdx.x & 31;
     const int sub = lane & (G - 1);  // lane within the vertex's group
     const int gw = lane / G;         // group within the warp
     const unsigned gmask = (unsigned)((1ull << G) - 1ull) << (gw * G);
     const int wbase = (tid - lane) / G;  // this warp's first group
     const int gstride = nthreads / G;
-    int prev_cnt = n, pass = 0;
     while (true) {
         uint64_t* bcur = a.b1 + (size_t)(pass & 1) * n;
         uint64_t* bold = a.b1 + (size_t)((pass + 1) & 1) * n;
@@ -270,7 +299,7 @@ __global__ void __launch_bounds__(kPaaThreads, 2) k_paa_sr(PaaArgs a) {
                 }
             }
         }
-        if (!grid_barrier(a.ctrl)) return;
+        if (!paa_barrier<CL>(a.ctrl)) return;
         const int cnt = *(volatile int*)&a.slots[pass];
         if (cnt == 0) break;
         for (int q0 = wbase; q0 < cnt; q0 += gstride) {
@@ -330,10 +359,14 @@ __global__ void __launch_bounds__(kPaaThreads, 2) k_paa_sr(PaaArgs a) {
                 cp[v] = 0ull;
             }
         }
-        if (!grid_barrier(a.ctrl)) return;
+        if (!paa_barrier<CL>(a.ctrl)) return;
         prev_cnt = cnt;
         if (++pass >= a.nslots) {
             if (tid == 0) atomicOr(&a.ctrl->err, kErrSlots);
+            return;
+        }
+        if (!CL && a.handoff > 0 && cnt <= a.handoff) {  // uniform: cnt is read after a barrier
+            if (tid == 0) a.ctrl->npasses = -(pass + 1);
             return;
         }
     }
@@ -427,6 +460,233 @@ __global__ void __launch_bounds__(kPaaBlockThreads, 1) k_paa_sr_block(PaaArgs a)
         }
     }
     if (t == 0) a.ctrl->npasses = pass;
+}
+
+// The same single-round passes on one thread-block cluster (levels of at most kPaaClMaxN
+// vertices whose data fit): block c owns the vertices [c chunk, (c + 1) chunk).  Every block
+// keeps full copies of cp and b1 and its own rows of the CSR (16-bit columns) in its shared
+// memory, so both sweeps read shared memory only; a block writes an entry into every block's
+// copy (distributed shared memory) only where it changes (b1 of its own vertices, cp of the
+// vertices its roots aggregate), a few entries per pass on these levels.  Cluster barriers
+// (release / acquire) separate the sweeps; each block's candidate count goes to every block
+// before the first, so every thread reads the total locally.  The sweeps read the same
+// snapshots as the grid version, so the passes, roots and aggregates are identical.
+constexpr int kPaaClThreads = 1024;
+constexpr int kPaaClMaxN = 12800;
+constexpr int kPaaClSmem = 220 * 1024;  // dynamic shared memory of a block, at most
+
+__device__ __forceinline__ uint32_t paa_map(const void* p, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void paa_bcast(unsigned long long* p, unsigned long long v, int C) {
+    for (int r = 0; r < C; r++)
+        asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(paa_map(p, r)), "l"(v) : "memory");
+}
+__device__ __forceinline__ void paa_bcast(int* p, int v, int C) {
+    for (int r = 0; r < C; r++)
+        asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(paa_map(p, r)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void paa_st(int* p, int rank, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(paa_map(p, rank)), "r"(v) : "memory");
+}
+constexpr int kPaaClBatch = 8;  // entries whose loads a lane issues together
+
+// max over the lane's entries k0 + sub, k0 + sub + G, ... < k1 of x[col[k]], the column
+// loads of kPaaClBatch entries issued together, then their gathers
+template <int G, typename CI>
+__device__ __forceinline__ unsigned long long paa_row_max(const CI* col, int k0, int k1, int sub,
+                                                          const unsigned long long* x) {
+    unsigned long long best = 0;
+    for (int k = k0 + sub; k < k1; k += G * kPaaClBatch) {
+        int u[kPaaClBatch];
+#pragma unroll
+        for (int b = 0; b < kPaaClBatch; b++) u[b] = k + b * G < k1 ? (int)col[k + b * G] : -1;
+#pragma unroll
+        for (int b = 0; b < kPaaClBatch; b++) {
+            const unsigned long long v = u[b] >= 0 ? x[u[b]] : 0ull;
+            best = v > best ? v : best;
+        }
+    }
+    return best;
+}
+
+// Updates a block queues per sweep before all its threads write them into every block
+// (a single thread writing one entry into 16 blocks serialises 16 remote stores).
+__host__ __device__ inline int paa_cl_evcap(int chunk) { return 2 * chunk + 64; }
+
+// Bytes of dynamic shared memory for a level (cp and b1; the two update queues; root, pass
+// and aggregate size of the block's vertices; its row offsets; up to `ecap` entries of its
+// rows).
+__host__ __device__ inline size_t paa_cl_bytes(int n, int chunk, int ecap) {
+    return 16 * (size_t)n + 20 * (size_t)paa_cl_evcap(chunk) + 12 * (size_t)chunk +
+           4 * (size_t)(chunk + 1) + ((2 * (size_t)ecap + 15) & ~(size_t)15);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kPaaClThreads, 1) k_paa_cl(PaaArgs a, int chunk, int ecap) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ int s_cnt[kPaaClThreads / 32];
+    __shared__ int s_part[16];  // the blocks' candidates of the pass, written by each block
+    __shared__ int s_nq1, s_nq2;  // queued updates of sweep 1 and sweep 2
+    const int n = a.n;
+    unsigned long long* cp = reinterpret_cast<unsigned long long*>(dyn);
+    unsigned long long* b1 = cp + n;
+    const int qcap = paa_cl_evcap(chunk);
+    unsigned long long* q1b = b1 + n;  // sweep 1: new b1 value of vertex q1w
+    int* q1w = reinterpret_cast<int*>(q1b + qcap);
+    int* q2u = q1w + qcap;  // sweep 2: vertex q2u joins the aggregate of root q2v
+    int* q2v = q2u + qcap;
+    // the block's vertices' root, pass and aggregate size, written to global memory at the
+    // end: global stores before a release barrier would make it wait for their completion
+    int* ro = q2v + qcap;
+    int* po = ro + chunk;
+    int* as = po + chunk;
+    int* rp = as + chunk;  // this block's row offsets
+    uint16_t* cl = reinterpret_cast<uint16_t*>(rp + chunk + 1);
+    const int C = (int)gridDim.x, rank = (int)blockIdx.x;  // the grid is one cluster
+    const int t = threadIdx.x;
+    const int r0 = min(rank * chunk, n), r1 = min(r0 + chunk, n), rows = r1 - r0;
+    const int e0 = a.rowptr[r0], E = a.rowptr[r1] - e0;
+    // a block whose rows exceed the capacity the host sized reads them from global memory
+    const bool staged = E <= ecap;
+    const int* gcl = a.col + e0;
+    for (int v = t; v < n; v += kPaaClThreads) {
+        cp[v] = a.prio[v];
+        b1[v] = 0ull;
+    }
+    for (int i = t; i <= rows; i += kPaaClThreads) rp[i] = a.rowptr[r0 + i] - e0;
+    if (staged)
+        for (int k = t; k < E; k += kPaaClThreads) cl[k] = (uint16_t)a.col[e0 + k];
+    for (int i = t; i < rows; i += kPaaClThreads) {
+        ro[i] = -1;
+        po[i] = -1;
+    }
+    if (t == 0) s_nq1 = s_nq2 = 0;
+    paa_cluster_barrier();  // every block's copies exist before any block writes into them
+    const int lane = t & 31, sub = lane & (G - 1);
+    const int g0 = t / G, gs = kPaaClThreads / G;  // this thread's group, groups per block
+    const int wg = g0 % (32 / G);                   // group within the warp
+    int pass = 0;
+    while (true) {
+        // sweep 1: b1[w] = max cp over N[w] for this block's w; count its candidates
+        int cnt = 0;
+        for (int q0 = g0 - wg; q0 < rows; q0 += gs) {  // uniform over the warp
+            const int q = q0 + wg;
+            const bool valid = q < rows;
+            const int k0 = valid ? rp[q] : 0, k1 = valid ? rp[q + 1] : 0;
+            unsigned long long best = staged ? paa_row_max<G>(cl, k0, k1, sub, cp)
+                                             : paa_row_max<G>(gcl, k0, k1, sub, cp);
+            best = group_max<G>(best);
+            if (valid && sub == 0) {
+                const int w = r0 + q;
+                if (best != b1[w]) {
+                    const int e = atomicAdd(&s_nq1, 1);
+                    if (e < qcap) {
+                        q1w[e] = w;
+                        q1b[e] = best;
+                    } else {
+                        paa_bcast(b1 + w, best, C);
+                    }
+                }
+                cnt += cp[w] != 0ull;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) s_cnt[t >> 5] = cnt;
+        __syncthreads();
+        if (t < 32) {
+            int c = s_cnt[t];
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (t == 0) paa_bcast(&s_part[rank], c, C);
+        }
+        {  // the queued b1 updates, one (entry, block) pair per thread
+            const int nq = min(s_nq1, qcap);
+            for (int j = t; j < nq * C; j += kPaaClThreads) {
+                const int e = j / C, r = j - e * C;
+                asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(paa_map(b1 + q1w[e], r)),
+                             "l"(q1b[e])
+                             : "memory");
+            }
+        }
+        paa_cluster_barrier();
+        if (t == 0) s_nq1 = 0;  // (sweep 1 of the next pass follows the next barrier)
+        int tot = 0;
+        for (int r = 0; r < C; r++) tot += s_part[r];
+        if (t == 0 && rank == 0) a.slots[pass] = tot;
+        if (tot == 0) break;
+        // sweep 2: a candidate whose priority tops max b1 over N[v] is a root and takes its
+        // unprocessed neighbours in ascending order, at most t-1
+        for (int q0 = g0 - wg; q0 < rows; q0 += gs) {
+            const int q = q0 + wg;
+            const int v = r0 + q;
+            const unsigned long long pv = q < rows ? cp[v] : 0ull;
+            const int k0 = pv ? rp[q] : 0, k1 = pv ? rp[q + 1] : 0;
+            unsigned long long m = staged ? paa_row_max<G>(cl, k0, k1, sub, b1)
+                                          : paa_row_max<G>(gcl, k0, k1, sub, b1);
+            m = group_max<G>(m);
+            if (!(pv != 0ull && m == pv && sub == 0)) continue;
+            int taken = 1;
+            for (int k = k0; k < k1; k++) {
+                const int u = staged ? (int)cl[k] : __ldg(gcl + k);
+                if (u == v) continue;
+                if (a.t > 0 && taken >= a.t) break;
+                if (cp[u] != 0ull) {
+                    const int e = atomicAdd(&s_nq2, 1);
+                    if (e < qcap) {
+                        q2u[e] = u;
+                        q2v[e] = v;
+                    } else {
+                        const int o = u / chunk, iu = u - o * chunk;  // u's block and row there
+                        paa_st(ro + iu, o, v);
+                        paa_st(po + iu, o, pass);
+                        paa_bcast(cp + u, 0ull, C);
+                    }
+                    taken++;
+                }
+            }
+            ro[q] = v;
+            po[q] = pass;
+            as[q] = taken;
+            const int e = atomicAdd(&s_nq2, 1);
+            if (e < qcap) {
+                q2u[e] = v;
+                q2v[e] = -1;  // the root itself: cp only
+            } else {
+                paa_bcast(cp + v, 0ull, C);
+            }
+        }
+        __syncthreads();
+        {  // the queued updates: cp = 0 in every block, root and pass in the owner's block
+            const int nq = min(s_nq2, qcap);
+            for (int j = t; j < nq * C; j += kPaaClThreads) {
+                const int e = j / C, r = j - e * C;
+                const int u = q2u[e];
+                asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(paa_map(cp + u, r)), "l"(0ull)
+                             : "memory");
+                const int o = u / chunk;
+                if (r == o && q2v[e] >= 0) {
+                    paa_st(ro + (u - o * chunk), o, q2v[e]);
+                    paa_st(po + (u - o * chunk), o, pass);
+                }
+            }
+        }
+        paa_cluster_barrier();
+        if (t == 0) s_nq2 = 0;  // (sweep 2 of the next pass follows the next barrier)
+        if (++pass >= a.nslots) {
+            if (t == 0 && rank == 0) atomicOr(&a.ctrl->err, kErrSlots);
+            return;
+        }
+    }
+    // every write into this block's ro / po preceded the last barrier
+    for (int i = t; i < rows; i += kPaaClThreads) {
+        a.root_of[r0 + i] = ro[i];
+        a.pass_of[r0 + i] = po[i];
+        if (ro[i] == r0 + i) a.agg_size[r0 + i] = as[i];
+    }
+    if (t == 0 && rank == 0) a.ctrl->npasses = pass;
 }
 
 // Maximal mode: every vertex per sweep, rounds of coarse-vertex selection then aggregation.
@@ -644,23 +904,177 @@ __global__ void __launch_bounds__(kPaaSmallThreads, 1) k_paa_small(PaaArgs a) {
 
 constexpr int kPaaLanesMaxN = 32768;  // largest level that shares lanes over a row
 
+constexpr int kPaaHandoff = 2048;  // candidates of a pass at which the cluster kernel takes over
+
+// Blocks of the cluster that continues the passes (16 where the device runs such a
+// cluster of k_paa_sr<G, true>, else 8, else 0: no hand-off).
 template <int G>
-static int launch_paa_sr(Handle* h, const PaaArgs& a, int* grid) {
+static int paa_cluster_blocks(int device) {
+    static DevCache cache;  // blocks + 1
+    int v = cache.get(device);
+    if (!v) {
+        int c = 0;
+        for (int want : {16, 8}) {
+            if (want > 8 && cudaFuncSetAttribute(k_paa_sr<G, true>,
+                                                 cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                                 1) != cudaSuccess)
+                continue;
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(want);
+            cfg.blockDim = dim3(kPaaThreads);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = want;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, k_paa_sr<G, true>, &cfg) == cudaSuccess && nc >= 1) {
+                c = want;
+                break;
+            }
+        }
+        cudaGetLastError();
+        v = c + 1;
+        cache.set(device, v);
+    }
+    return v - 1;
+}
+
+// The cooperative grid kernel, then (where the device runs the cluster) the cluster kernel
+// that takes over once a pass has at most kPaaHandoff candidates; the cluster kernel returns
+// at once when the grid kernel finished.  Counts its launches.
+template <int G>
+static int launch_paa_sr(Handle* h, const PaaArgs& a0, int* grid) {
     static DevCache occ;
     int blocks_per_sm = occ.get(h->device);
     if (!blocks_per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_paa_sr<G>,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_paa_sr<G, false>,
                                                           kPaaThreads, 0) != cudaSuccess ||
             blocks_per_sm < 1)
             blocks_per_sm = 1;
         occ.set(h->device, blocks_per_sm);
     }
     *grid = blocks_per_sm * h->num_sms;
-    const int need = grid_for((long long)a.n * G, kPaaThreads);
+    const int need = grid_for((long long)a0.n * G, kPaaThreads);
     if (*grid > need) *grid = need;
-    void* args[] = {const_cast<PaaArgs*>(&a)};
-    return check_cuda(cudaLaunchCooperativeKernel((const void*)k_paa_sr<G>, dim3(*grid),
-                                                  dim3(kPaaThreads), args, 0, h->work));
+    const int C = paa_cluster_blocks<G>(h->device);
+    PaaArgs a = a0;
+    a.handoff = C ? kPaaHandoff : 0;
+    int st = check_cuda(cudaMemsetAsync(&h->ctrl->npasses, 0, sizeof(int), h->work));
+    if (st) return st;
+    void* args[] = {&a};
+    st = check_cuda(cudaLaunchCooperativeKernel((const void*)k_paa_sr<G, false>, dim3(*grid),
+                                                dim3(kPaaThreads), args, 0, h->work));
+    count_launch(h);
+    if (st || !C) return st;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kPaaThreads);
+    cfg.stream = h->work;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    a.handoff = 0;
+    st = check_cuda(cudaLaunchKernelEx(&cfg, k_paa_sr<G, true>, a));
+    count_launch(h);
+    return st;
+}
+
+// Blocks of the cluster for k_paa_cl (16 where the device runs such a cluster with the
+// largest shared memory, else 8, else 0) and the attributes, once per device.
+static int paa_cl_blocks(int device) {
+    static DevCache cache;  // blocks + 1
+    int v = cache.get(device);
+    if (!v) {
+        const int smem = kPaaClSmem;
+        int c = 0;
+        bool ok = true;
+        auto attrs = [&](auto k) {
+            ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                           cudaSuccess;
+            cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        };
+        attrs(k_paa_cl<1>);
+        attrs(k_paa_cl<2>);
+        attrs(k_paa_cl<4>);
+        attrs(k_paa_cl<8>);
+        attrs(k_paa_cl<16>);
+        attrs(k_paa_cl<32>);
+        for (int want : {16, 8}) {
+            if (!ok) break;
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(want);
+            cfg.blockDim = dim3(kPaaClThreads);
+            cfg.dynamicSmemBytes = smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = want;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, k_paa_cl<1>, &cfg) == cudaSuccess && nc >= 1) {
+                c = want;
+                break;
+            }
+        }
+        cudaGetLastError();
+        v = c + 1;
+        cache.set(device, v);
+    }
+    return v - 1;
+}
+
+// Entry capacity of a block's rows for k_paa_cl: twice the mean share (rows of these levels
+// are within a small factor of the mean length), limited by the shared memory; 0 when the
+// level does not fit.
+static int paa_cl_ecap(int n, long long nnz, int C) {
+    const int chunk = (n + C - 1) / C;
+    long long ecap = 2 * ((nnz + C - 1) / C) + 256;
+    if (ecap > nnz) ecap = nnz;
+    const size_t fixed = paa_cl_bytes(n, chunk, 0);
+    if (fixed >= (size_t)kPaaClSmem) return 0;
+    const long long room = ((long long)kPaaClSmem - (long long)fixed) / 2;
+    if (ecap > room) return 0;  // would not fit with the bound: the grid kernel runs instead
+    return (int)ecap;
+}
+
+// k_paa_cl on a cluster of C blocks, G lanes per vertex: as many lanes as leave every block's
+// vertices one group each, up to the mean row length.
+static int launch_paa_cl(Handle* h, const PaaArgs& a, long long nnz, int C, int ecap) {
+    const int chunk = (a.n + C - 1) / C;
+    const long long avg = a.n > 0 ? (nnz + a.n - 1) / a.n : 1;
+    int G = 1;
+    while (G < 32 && (long long)chunk * G * 2 <= kPaaClThreads && G * 2 <= avg) G *= 2;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kPaaClThreads);
+    cfg.dynamicSmemBytes = paa_cl_bytes(a.n, chunk, ecap);
+    cfg.stream = h->work;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    switch (G) {
+        case 1: e = cudaLaunchKernelEx(&cfg, k_paa_cl<1>, a, chunk, ecap); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, k_paa_cl<2>, a, chunk, ecap); break;
+        case 4: e = cudaLaunchKernelEx(&cfg, k_paa_cl<4>, a, chunk, ecap); break;
+        case 8: e = cudaLaunchKernelEx(&cfg, k_paa_cl<8>, a, chunk, ecap); break;
+        case 16: e = cudaLaunchKernelEx(&cfg, k_paa_cl<16>, a, chunk, ecap); break;
+        default: e = cudaLaunchKernelEx(&cfg, k_paa_cl<32>, a, chunk, ecap); break;
+    }
+    return check_cuda(e);
 }
 
 int launch_paa(Handle* h, int level, int n, long long nnz, const int* rowptr, const int* col,
@@ -688,9 +1102,14 @@ int launch_paa(Handle* h, int level, int n, long long nnz, const int* rowptr, co
         cudaEventRecord(ps.a, h->work);
     }
     int st = UAAMG_OK;
+    bool counted = false;
     const bool u16 = n <= 65536;
     const size_t blk_bytes = u16 ? paa_block_bytes<uint16_t>(n, nnz) : paa_block_bytes<int>(n, nnz);
-    if (mode == UAAMG_PASS_SINGLE_ROUND && n <= kPaaBlockMaxN && blk_bytes <= kPaaBlockSmem) {
+    const int ccl = mode == UAAMG_PASS_SINGLE_ROUND && n <= kPaaClMaxN ? paa_cl_blocks(h->device) : 0;
+    const int ecap = ccl ? paa_cl_ecap(n, nnz, ccl) : 0;
+    if (ecap > 0) {  // the level in the shared memory of one cluster
+        st = launch_paa_cl(h, a, nnz, ccl, ecap);
+    } else if (mode == UAAMG_PASS_SINGLE_ROUND && n <= kPaaBlockMaxN && blk_bytes <= kPaaBlockSmem) {
         // the whole level in one block's shared memory
         static DevCache attr;
         if (!attr.get(h->device)) {
@@ -714,6 +1133,7 @@ int launch_paa(Handle* h, int level, int n, long long nnz, const int* rowptr, co
         else if (avg <= 8) st = launch_paa_sr<8>(h, a, &grid);
         else if (avg <= 16) st = launch_paa_sr<16>(h, a, &grid);
         else st = launch_paa_sr<32>(h, a, &grid);
+        counted = true;  // the launcher counts its launches
     } else {
         static DevCache occ;
         int blocks_per_sm = occ.get(h->device);
@@ -735,7 +1155,7 @@ int launch_paa(Handle* h, int level, int n, long long nnz, const int* rowptr, co
         cudaEventRecord(ps.b, h->work);
         h->prof_slots.push_back(ps);
     }
-    count_launch(h);
+    if (!counted) count_launch(h);
     return st;
 }
 

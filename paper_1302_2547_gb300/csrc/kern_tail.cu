@@ -329,11 +329,11 @@ __host__ __device__ inline void dsm_layout(DsmHead& H, int nl, int tsize, const 
     };
     for (int i = 0; i < nl; i++) {
         DsmLev& D = H.lv[i];
+        D.streamed = (streamed_mask >> i) & 1;
         if (i == nl - 1) {
-            if (!D.inv_global) D.val = take(8LL * D.rows * D.n);
+            if (!D.inv_global && !D.streamed) D.val = take(8LL * D.rows * D.n);
             continue;
         }
-        D.streamed = (streamed_mask >> i) & 1;
         D.rp = take(4LL * (D.chunk + 1));
         if (!D.streamed) {
             D.col = take(2LL * cnt[i].E);
@@ -346,9 +346,13 @@ __host__ __device__ inline void dsm_layout(DsmHead& H, int nl, int tsize, const 
         D.mem = take(2LL * cnt[i].M);
     }
     H.staged = off > (1LL << 30) ? (1 << 30) : (int)off;
-    for (int i = 0; i < nl - 1; i++) {
+    for (int i = 0; i < nl; i++) {
         DsmLev& D = H.lv[i];
         if (!D.streamed) continue;
+        if (i == nl - 1) {  // the coarsest inverse rows, read through L2
+            if (!D.inv_global) D.val = take(8LL * D.rows * D.n);
+            continue;
+        }
         D.col = take(2LL * cnt[i].E);
         D.agg = take(2LL * cnt[i].E);
         D.val = take((long long)tsize * cnt[i].E);
@@ -554,7 +558,6 @@ __global__ void __launch_bounds__(kDsmThreads, 1)
 k_tail_dsm(const unsigned char* __restrict__ blob, long long stride, int copy16, int vb, int m0,
            int nlev, const double* __restrict__ inv, double tau, const T* __restrict__ rhs_g,
            T* __restrict__ out_g, const int* skip) {
-    if (skip && *(volatile const int*)skip) return;  // uniform over the cluster
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ DsmFrame st[2 * kDsmMaxLev];
     __shared__ int sp;
@@ -573,6 +576,9 @@ k_tail_dsm(const unsigned char* __restrict__ blob, long long stride, int copy16,
                          : "memory");
         asm volatile("cp.async.wait_all;" ::: "memory");
     }
+    // the region is setup data; what the preceding kernels write is read from here on
+    pdl_wait();
+    if (skip && *(volatile const int*)skip) return;  // uniform over the cluster
     __syncthreads();
     const unsigned char* staged = sm + vb;
     const DsmHead& H = *(const DsmHead*)staged;
@@ -581,9 +587,10 @@ k_tail_dsm(const unsigned char* __restrict__ blob, long long stride, int copy16,
         T* rho = (T*)(sm + L.vec[DV_RHS]);
         for (int i = tid; i < L.rows; i += kDsmThreads) rho[i] = rhs_g[L.row0 + i];
     }
-    if (tid == 0) {
-        st[0] = DsmFrame{0, m0, 0, DV_RHS, DV_SE, 0.0, 0.0, 0.0};
-        sp = 1;
+    if (tid == 0) {  // K_m0, with its first step's B_m0 already pushed
+        st[0] = DsmFrame{0, m0, 1, DV_RHS, DV_SE, 0.0, 0.0, 0.0};
+        st[1] = DsmFrame{1, m0, 0, DV_RHS, DV_C1, 0.0, 0.0, 0.0};
+        sp = 2;
     }
     int slot = 0;
     __syncthreads();
@@ -599,7 +606,7 @@ k_tail_dsm(const unsigned char* __restrict__ blob, long long stride, int copy16,
             return (T*)(sm + L.vec[v]) + (dsm_replicated(v, coarsest) ? L.row0 : 0);
         };
         int push = 0, pop = 0, next_phase = f.phase;
-        DsmFrame child{};
+        DsmFrame child{}, child2{};  // push = 2: child2 goes on top of child
         double rho1 = f.rho1, w1 = f.w1, w2 = f.w2;
         bool cluster_end = false;  // the phase's rows are read by other blocks next
         if (coarsest) {  // exact solve with the dense inverse, a warp per row
@@ -612,7 +619,8 @@ k_tail_dsm(const unsigned char* __restrict__ blob, long long stride, int copy16,
                 bool done = false;
                 if constexpr (sizeof(T) == 4) {
                     if (!L.inv_global) {  // FP32 pairs hi + lo of the inverse, FP32-pair sums
-                        const float2* row = (const float2*)(staged + L.val) + (size_t)i * L.n;
+                        const float2* row =
+                            (const float2*)((L.streamed ? region : staged) + L.val) + (size_t)i * L.n;
                         FF a{0.f, 0.f};
                         for (int j = lane; j < L.n; j += 32) {
                             const float2 w = row[j];
@@ -626,7 +634,8 @@ k_tail_dsm(const unsigned char* __restrict__ blob, long long stride, int copy16,
                 }
                 if (!done) {
                     const double* row = L.inv_global ? inv + (size_t)(L.row0 + i) * L.n
-                                                     : (const double*)(staged + L.val) + (size_t)i * L.n;
+                                                     : (const double*)((L.streamed ? region : staged) + L.val) +
+                                                           (size_t)i * L.n;
                     double sum = 0.0;
                     for (int j = lane; j < L.n; j += 32) sum = fma(row[j], (double)b[j], sum);
                     sum = warp_sum(sum);
@@ -756,8 +765,14 @@ k_tail_dsm(const unsigned char* __restrict__ blob, long long stride, int copy16,
                     if (child_coarsest) bcast(rc + I, sum, C);  // the dense solve reads it all
                     else rc[I] = sum;
                 }
-                child = DsmFrame{0, f.level + 1, 0, DV_RHS, DV_SE, 0.0, 0.0, 0.0};
-                push = 1;
+                if (child_coarsest) {
+                    child = DsmFrame{0, f.level + 1, 0, DV_RHS, DV_SE, 0.0, 0.0, 0.0};
+                    push = 1;
+                } else {  // K_{l+1} at its first step, with that step's B_{l+1} on top
+                    child = DsmFrame{0, f.level + 1, 1, DV_RHS, DV_SE, 0.0, 0.0, 0.0};
+                    child2 = DsmFrame{1, f.level + 1, 0, DV_RHS, DV_C1, 0.0, 0.0, 0.0};
+                    push = 2;
+                }
                 next_phase = 1;
             } else {  // out = x' + Minv (in - A x'), x' = x + P e_c
                 const T* ec = (const T*)(sm + Lc.vec[DV_SE]);
@@ -782,10 +797,9 @@ k_tail_dsm(const unsigned char* __restrict__ blob, long long stride, int copy16,
                 st[top - 1].rho1 = rho1;
                 st[top - 1].w1 = w1;
                 st[top - 1].w2 = w2;
-                if (push) {
-                    st[top] = child;
-                    sp = top + 1;
-                }
+                if (push) st[top] = child;
+                if (push == 2) st[top + 1] = child2;
+                sp = top + push;
             }
         }
         __syncthreads();
@@ -1046,8 +1060,14 @@ static int tail_prepare_t(Handle* h, int m_first) {
             }
         }
         if (vb >= dyn) continue;
-        for (int ns = 0; ns < nl - 1 && !best_m0; ns++) {
-            const unsigned mask = (1u << ns) - 1u;
+        // what streams, in order of preference: nothing; the coarsest inverse; that and the
+        // per-entry arrays of the top levels, one more level at a time
+        unsigned masks[kDsmMaxLev + 1];
+        int nm = 0;
+        masks[nm++] = 0u;
+        for (int ns = 0; ns < nl - 1; ns++) masks[nm++] = (1u << (nl - 1)) | ((1u << ns) - 1u);
+        for (int mi = 0; mi < nm && !best_m0; mi++) {
+            const unsigned mask = masks[mi];
             int staged = 0;
             long long total = 0;
             for (int c = 0; c < C; c++) {
@@ -1121,13 +1141,17 @@ int launch_tail(Handle* h, int m0) {
     cfg.blockDim = dim3(kDsmThreads);
     cfg.dynamicSmemBytes = h->tail_smem;
     cfg.stream = h->work;
-    cudaLaunchAttribute at[1];
+    // programmatic serialization: the launch and the staging of the region overlap the
+    // preceding kernel, which the kernel waits for before it reads its input
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = h->tail_cl;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     const Level& L = h->lev[m0];
     cudaError_t e = cudaLaunchKernelEx(&cfg, k_tail_dsm<T>, (const unsigned char*)h->tail_blob,
                                        h->tail_stride, h->tail_copy / 16, h->tail_vb, m0, h->nlev,
