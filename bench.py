@@ -68,14 +68,15 @@ NCU_SOURCES = {
 }
 NCU_TRAFFIC = {
     # level 0 of the 128^3 system, ncu --set full (one capture per launch)
-    # k_rowwarp_tma<float, RB_PRE1>: 141,836,544 + 8,271,104 bytes
-    ("smooth0", "118ce82ac812d088"): 150107648,
-    # k_rowwarp_tma<double, RB_SPMV, 2 dots>: 216,965,888 + 12,919,296 bytes
-    ("spmv64", "118ce82ac812d088"): 229885184,
-    # k_paa_sr<1> on level 0 (one launch, every pass): 1.88395 GB + 560,823,040 bytes
-    ("paa", "b55b623873278b85"): 2444773040,
-    # k_coarse_build on level 0 (first stage): 266,696,000 + 109,914,624 bytes
-    ("coarse", "b55b623873278b85"): 376610624,
+    # k_rowwarp_tma<float, RB_PRE1>: 141,837,568 + 8,121,088 bytes
+    ("smooth0", "765f19d13a4424fd"): 149958656,
+    # k_rowwarp_tma<double, RB_SPMV, 2 dots>: 216,966,144 + 12,837,376 bytes
+    ("spmv64", "765f19d13a4424fd"): 229803520,
+    # level 0's aggregation: k_paa_sr<1, grid> 1.918927 GB + 564,222,208 bytes, then the
+    # cluster continuation k_paa_sr<1, cluster> 632 KB read
+    ("paa", "91724f4a79b43d55"): 2483781208,
+    # k_coarse_build on level 0 (first stage): 266,640,128 + 110,002,432 bytes
+    ("coarse", "91724f4a79b43d55"): 376642560,
 }
 
 
