@@ -468,7 +468,7 @@ __device__ __forceinline__ void dsm_sum(const A (&v)[ND], double (&out)[ND], A (
     if (wid == 0) {
 #pragma unroll
         for (int k = 0; k < ND; k++) {
-            const A s = acc_warp(sh[k][lane]);
+            const A s = acc_warp(lane < kDsmThreads / 32 ? sh[k][lane] : A{});
             if (lane == 0) part[slot][k] = s;
         }
     }
