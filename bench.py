@@ -68,10 +68,10 @@ NCU_SOURCES = {
 }
 NCU_TRAFFIC = {
     # level 0 of the 128^3 system, ncu --set full (one capture per launch)
-    # k_rowwarp_tma<float, RB_PRE1>: 141,837,568 + 8,121,088 bytes
-    ("smooth0", "765f19d13a4424fd"): 149958656,
-    # k_rowwarp_tma<double, RB_SPMV, 2 dots>: 216,966,144 + 12,837,376 bytes
-    ("spmv64", "765f19d13a4424fd"): 229803520,
+    # k_rowwarp_tma<float, RB_PRE1>: 141,839,872 + 8,072,704 bytes
+    ("smooth0", "07a13fea71c8c66f"): 149912576,
+    # k_rowwarp_tma<double, RB_SPMV, 2 dots>: 216,978,176 + 12,235,520 bytes
+    ("spmv64", "07a13fea71c8c66f"): 229213696,
     # level 0's aggregation: k_paa_sr<1, grid> 1.918927 GB + 564,222,208 bytes, then the
     # cluster continuation k_paa_sr<1, cluster> 632 KB read
     ("paa", "91724f4a79b43d55"): 2483781208,

@@ -3,7 +3,7 @@
 //
 // A persistent grid; every warp walks its own chunks of 32 rows, c = w, w + W, ... (W warps
 // in the grid).  The entries of a chunk are one contiguous range of col/val.  Lane 0 of the
-// warp copies the ranges of the warp's next two chunks into the warp's own two-stage
+// warp copies the ranges of the warp's next kTmaStages chunks into the warp's own
 // shared-memory ring with 1D bulk copies (cp.async.bulk ... mbarrier::complete_tx), so the
 // HBM stream of the matrix runs ahead of the computation.  Each lane then walks its own row
 // in the staged arrays, gathering the vector entries eight at a time, adds the row in stored
@@ -22,6 +22,12 @@ namespace uaamg {
 constexpr int kTmaWarps = kThreads / 32;   // warps per block, each with its own pipeline
 constexpr int kTmaBatch = 8;               // gathers a lane has in flight per row
 constexpr long long kTmaSpin = 1LL << 31;  // clock cycles before a stage wait gives up (default)
+// Chunks a warp has staged or in flight, and the stage entries for rows of about 7 entries.
+// The kernel is bound by the latency of its vector gathers, so resident warps count more
+// than ring depth: with two stages of 232 entries, seven FP32 blocks fit an SM (six with
+// 256 entries, four or five with three stages).
+constexpr int kTmaStages = 2;
+constexpr int kTmaShortCap = 232;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -54,13 +60,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         : "memory");
 }
 
-// One warp's two stages of CAP entries each.
+// One warp's stages of CAP entries each (CAP a multiple of 4: every array starts on 16 bytes).
 template <typename T, int CAP>
-struct WarpStages {
-    int col[2][CAP];
-    T val[2][CAP];
-    uint64_t bar[2];
+struct alignas(16) WarpStages {
+    int col[kTmaStages][CAP];
+    T val[kTmaStages][CAP];
+    uint64_t bar[kTmaStages];
 };
+static_assert(kTmaShortCap % 4 == 0 && kTmaStages >= 2, "stages start on 16 bytes");
+static_assert(sizeof(WarpStages<double, 512>) * kTmaWarps <= 227 * 1024, "ring fits a block");
 
 // Lane 0: copies of the entry range [k0, k1) into stage s; false when it does not fit.
 template <typename T, int CAP>
@@ -113,10 +121,9 @@ __global__ void __launch_bounds__(kThreads) k_rowwarp_tma(RBArgs<T> a, Ctrl* ctr
     const int gw = blockIdx.x * kTmaWarps + warp;
     unsigned staged = 0;  // bit s: stage s holds its chunk (lane 0's copy, broadcast)
     if (lane == 0) {
-        mbar_init(&ws.bar[0], 1);
-        mbar_init(&ws.bar[1], 1);
+        for (int s = 0; s < kTmaStages; s++) mbar_init(&ws.bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < kTmaStages; s++) {
             const int c = gw + s * W;
             if (c < nch && tma_issue<T, CAP>(a, ws, a.rowptr[c << 5],
                                              a.rowptr[min(a.n, (c + 1) << 5)], s))
@@ -132,11 +139,11 @@ __global__ void __launch_bounds__(kThreads) k_rowwarp_tma(RBArgs<T> a, Ctrl* ctr
     for (int it = 0;; it++) {
         const int c = gw + it * W;
         if (c >= nch) break;
-        const int s = it & 1;
+        const int s = it % kTmaStages;
         const int r0 = c << 5, r1 = min(a.n, r0 + 32);
         const int row = r0 + lane;
         // lane 0 loads the bounds of the chunk it copies into this stage next
-        const int nc = c + 2 * W;
+        const int nc = c + kTmaStages * W;
         int nk0 = 0, nk1 = 0;
         if (lane == 0 && nc < nch) {
             nk0 = a.rowptr[nc << 5];
@@ -164,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_rowwarp_tma(RBArgs<T> a, Ctrl* ctr
                 if (lane == 0) {
                     atomicOr(&ctrl->err, kErrTimeout);
                     // let the copies still in flight land before this warp stops using them
-                    for (int q = 0; q < 2; q++) {
+                    for (int q = 0; q < kTmaStages; q++) {
                         if (!((staged >> q) & 1u)) continue;
                         const long long t1 = clock64();
                         while (!mbar_try_wait(&ws.bar[q], (phase >> q) & 1u) &&
@@ -234,11 +241,11 @@ static int launch_cap(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
 }
 
 // Stage size from the average row length: a chunk of 32 rows of a 7-point stencil (224
-// entries plus up to 6 of alignment) fits 256 entries; longer rows take 512.
+// entries plus up to 6 of alignment) fits kTmaShortCap entries; longer rows take 512.
 template <typename T>
 int launch_rowblock_tma(Handle* h, int mode, int ndots, const RBArgs<T>& a) {
     const bool short_rows = a.n > 0 && a.nnz > 0 && a.nnz * 4 <= (long long)a.n * 29;
-    return short_rows ? launch_cap<T, 256>(h, mode, ndots, a)
+    return short_rows ? launch_cap<T, kTmaShortCap>(h, mode, ndots, a)
                       : launch_cap<T, 512>(h, mode, ndots, a);
 }
 template int launch_rowblock_tma<float>(Handle*, int, int, const RBArgs<float>&);
