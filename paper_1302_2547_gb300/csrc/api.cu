@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "pinned.cuh"
 #include "kernels.cuh"
 
 namespace uaamg {
@@ -49,7 +50,7 @@ static void destroy(Handle* h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->loop_graph) cudaGraphExecDestroy(h->loop_graph);
     if (h->mgraph) cudaGraphExecDestroy(h->mgraph);
-    if (h->mos_host) cudaFreeHost(h->mos_host);
+    pinned_put(h->mos_host);
     for (auto& ps : h->prof_slots) {
         cudaEventDestroy(ps.a);
         cudaEventDestroy(ps.b);
@@ -59,7 +60,7 @@ static void destroy(Handle* h) {
         cudaStreamSynchronize(h->work);
         cudaStreamDestroy(h->work);
     }
-    if (h->osc_host) cudaFreeHost(h->osc_host);
+    pinned_put(h->osc_host);
     cudaEvent_t evs[] = {h->ev_in, h->ev_out, h->ev_t0, h->ev_t1};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);

@@ -1,4 +1,5 @@
-// runtime.cu -- device-memory pool, budget accounting, launch counters, status strings.
+// runtime.cu -- device-memory pool, page-locked host blocks, budget accounting, launch
+// counters, status strings.
 //
 // All device memory of a handle comes from a per-device CUDA memory pool owned by the
 // library (stream-ordered allocation on the handle's stream, release threshold = never),
@@ -6,8 +7,11 @@
 // library-wide byte budget lets a serving layer admit work by device memory.
 #include <atomic>
 #include <mutex>
+#include <unordered_map>
+#include <vector>
 
 #include "common.cuh"
+#include "pinned.cuh"
 
 namespace uaamg {
 
@@ -38,6 +42,40 @@ static cudaMemPool_t pool_for(int dev) {
         g_pool_ok[dev] = true;
     }
     return g_pool[dev];
+}
+
+// ---- page-locked host blocks (pinned.cuh) --------------------------------------------------
+static std::mutex g_pin_mu;
+static std::vector<void*> g_pin_free[48];           // free blocks by size class 2^c
+static std::unordered_map<void*, int> g_pin_class;  // every block handed out, by class
+
+void* pinned_get(size_t bytes) {
+    int c = 8;  // 256 bytes at least
+    while (c < 47 && ((size_t)1 << c) < bytes) c++;
+    if (((size_t)1 << c) < bytes) return nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (!g_pin_free[c].empty()) {
+            void* p = g_pin_free[c].back();
+            g_pin_free[c].pop_back();
+            return p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, (size_t)1 << c) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_class[p] = c;
+    return p;
+}
+
+void pinned_put(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    auto it = g_pin_class.find(p);
+    if (it != g_pin_class.end()) g_pin_free[it->second].push_back(p);
 }
 
 void* dalloc_bytes(Handle* h, size_t bytes, int* status, bool temp) {

@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "pinned.cuh"
 #include "kern_sra.cuh"
 #include "kernels.cuh"
 
@@ -152,7 +153,8 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
     const bool mixed = (h->p.precision == UAAMG_MIXED);
     const bool twice = (h->p.agg_repeat == 2);
     HostReadback* hb = nullptr;
-    if (cudaMallocHost(&hb, sizeof(HostReadback)) != cudaSuccess) return UAAMG_ERR_OOM;
+    hb = static_cast<HostReadback*>(pinned_get(sizeof(HostReadback)));
+    if (!hb) return UAAMG_ERR_OOM;
     memset(hb, 0, sizeof(HostReadback));
 
     h->ctrl = dalloc<Ctrl>(h, 1, &st);
@@ -347,7 +349,8 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
             }
             if (st) goto done;
         }
-        if (cudaMallocHost(&h->osc_host, sizeof(OuterScalars)) != cudaSuccess) st = UAAMG_ERR_OOM;
+        h->osc_host = static_cast<OuterScalars*>(pinned_get(sizeof(OuterScalars)));
+        if (!h->osc_host) st = UAAMG_ERR_OOM;
     }
     {  // levels small enough for a fused K-cycle kernel (one pre- and post-sweep only): the
         // cluster kernel where its levels fit in the cluster's shared memory, else one block
@@ -407,7 +410,8 @@ int build_hierarchy(Handle* h, const uaamg_csr* A) {
     if (st == UAAMG_OK && h->p.autotune) st = autotune_levels(h);
 done:
     dfree_temps(h);
-    if (hb) cudaFreeHost(hb);
+    cudaStreamSynchronize(h->work);  // no readback into hb is still in flight
+    pinned_put(hb);
     return st;
 }
 

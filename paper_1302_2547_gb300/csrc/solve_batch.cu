@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "pinned.cuh"
 #include "kernels.cuh"
 
 namespace uaamg {
@@ -353,7 +354,8 @@ int solve_batch(Handle* const* hs, int nsys, const int* R, const double* const* 
     bt.d_os = dalloc<double>(&bt.bh, (size_t)os_off[nsys], &st);
     bt.partials = dalloc<double>(&bt.bh, (size_t)plan.max_part, &st);
     bt.counters = dalloc<unsigned int>(&bt.bh, nsys, &st);
-    if (st == UAAMG_OK && cudaMallocHost(&bt.h_os, sizeof(double) * os_off[nsys]) != cudaSuccess)
+    if (st == UAAMG_OK &&
+        !(bt.h_os = static_cast<double*>(pinned_get(sizeof(double) * os_off[nsys]))))
         st = UAAMG_ERR_OOM;
     std::vector<int> h_active(nsys, 1);
     std::vector<int4> h_chk;
@@ -368,7 +370,7 @@ int solve_batch(Handle* const* hs, int nsys, const int* R, const double* const* 
         if (bt.graph) cudaGraphExecDestroy(bt.graph);
         dfree_all(&bt.bh);
         cudaStreamSynchronize(ws);
-        if (bt.h_os) cudaFreeHost(bt.h_os);
+        pinned_put(bt.h_os);
         for (cudaEvent_t e : evs) cudaEventDestroy(e);
         cudaStreamDestroy(ws);
         cudaGetLastError();

@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "pinned.cuh"
 #include "kernels.cuh"
 
 namespace uaamg {
@@ -85,10 +86,11 @@ int ensure_multi(Handle* h, int R) {
     if (st) return st;
     if (h->mos_host) {
         cudaStreamSynchronize(h->work);
-        cudaFreeHost(h->mos_host);
+        pinned_put(h->mos_host);
         h->mos_host = nullptr;
     }
-    if (cudaMallocHost(&h->mos_host, sizeof(double) * 8 * R) != cudaSuccess) return UAAMG_ERR_OOM;
+    h->mos_host = static_cast<double*>(pinned_get(sizeof(double) * 8 * R));
+    if (!h->mos_host) return UAAMG_ERR_OOM;
     h->multi_R = R;
     return UAAMG_OK;
 }
