@@ -31,8 +31,18 @@ TOL = 1e-8
 WORKLOAD = "laplace3d_128^3 7-point, Dirichlet, lognormal(0.25) edge weights"
 # Method parameters of this workload: aggregates of at most 4 vertices, aggregation applied
 # twice per level (Section 3.3), one flexible-CG step on levels reached by coarsening
-# weaker than 5x, and a small level that shrinks by less than 1.5x becomes the coarsest.
-BENCH_PARAMS = dict(max_agg_size=4, agg_repeat=2, kcycle_ratio=5.0, min_coarsening=1.5)
+# weaker than 6x, and a small level that shrinks by less than 1.5x becomes the coarsest.
+# (With 5x the 29,839 -> 5,465 level takes two steps: 34 iterations instead of 39, but a
+# slower solve, 30.1 against 26.8 ms.)
+BENCH_PARAMS = dict(max_agg_size=4, agg_repeat=2, kcycle_ratio=6.0, min_coarsening=1.5)
+# The 3D grids with lognormal weights of the serving stream coarsen their first level by only
+# 5.6-5.8x, so they keep ratio 5 (with 6 that level takes one step: 45-54 iterations instead
+# of 26-30 from 2e5 to 7e5 unknowns).
+GRID3D_PARAMS = dict(BENCH_PARAMS, kcycle_ratio=5.0)
+# 16 right-hand sides of the headline system per setup: the multi-column cycle is bound by
+# its matrix and vector traffic, so the second step on the 5.5x level pays for itself there
+# (ratio 5: fewer iterations at a slightly dearer cycle).
+MULTI_RHS_PARAMS = dict(BENCH_PARAMS, kcycle_ratio=5.0)
 # The unstructured workload (4M-point random geometric graph, mean degree 8): aggregates of
 # unbounded size, one aggregation per level, one K-cycle step below 3x coarsening.  With a
 # size limit the coarse levels of this graph stall (about 2% per level below a few
@@ -176,7 +186,7 @@ CLUSTER_BELOW = None  # --cluster-below: levels of at most this many rows run on
 AUTOTUNE = None  # --autotune 0/1: time the kernel families per level at setup
 
 
-def bench_params(U, precision, profile_class=0):
+def bench_params(U, precision, profile_class=0, base=None):
     extra = {} if TMA_ROWS is None else {"tma_rows": TMA_ROWS}
     if FUSE_BELOW is not None:
         extra["fuse_below"] = FUSE_BELOW
@@ -187,7 +197,7 @@ def bench_params(U, precision, profile_class=0):
     if AUTOTUNE is not None:
         extra["autotune"] = AUTOTUNE
     return U.uaamg_default_params(precision=precision, profile_class=profile_class,
-                                  use_graphs=0 if EAGER else 1, **BENCH_PARAMS, **extra)
+                                  use_graphs=0 if EAGER else 1, **(base or BENCH_PARAMS), **extra)
 
 
 _LAST_X = {}  # the headline solve's solution, compared with the oracle's on rank 0
@@ -282,7 +292,8 @@ def run_gpu(args, rank, world):
         brec = []
 
         def batched_step():
-            h = U.uaamg_setup(rp, cc, vv, bench_params(U, U.UAAMG_MIXED), stream=stream)
+            h = U.uaamg_setup(rp, cc, vv, bench_params(U, U.UAAMG_MIXED, base=MULTI_RHS_PARAMS),
+                              stream=stream)
             try:
                 st, its, rrs = U.uaamg_solve_many(h, Bb, Xb, TOL)
                 if st != 0:
@@ -309,7 +320,7 @@ def run_gpu(args, rank, world):
         worst = max(float(np.linalg.norm(Bh[:, r] - Asp0 @ Xh[:, r]) / np.linalg.norm(Bh[:, r]))
                     for r in range(R))
         batched = {"value": round(R * Kb * world / job_time(tb, world, dev), 3), "unit": "solves/s",
-                   "rhs_per_setup": R, "steps": Kb,
+                   "rhs_per_setup": R, "steps": Kb, "params": MULTI_RHS_PARAMS,
                    "setup_ms": round(float(np.median([r[2]["setup_ms"] for r in brec])), 3),
                    "solve_ms": round(float(np.median([r[2]["solve_ms"] for r in brec])), 3),
                    "iterations_max": int(max(r[0] for r in brec)),
@@ -833,7 +844,7 @@ def run_serving(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
     logs = {k: np.log([b[1] for b in bases if b[0] == k]) for k in range(3)}
     by_kind = {k: [b[2] for b in bases if b[0] == k] for k in range(3)}
     # one service per kind, each with that kind's method parameters and a third of the budget
-    params = [U.uaamg_default_params(**C4_GRID2D_PARAMS), U.uaamg_default_params(**BENCH_PARAMS),
+    params = [U.uaamg_default_params(**C4_GRID2D_PARAMS), U.uaamg_default_params(**GRID3D_PARAMS),
               U.uaamg_default_params(**RGG_PARAMS)]
     rng = np.random.default_rng(seed)
     next_key = [1]
@@ -896,6 +907,7 @@ def run_serving(n_requests=2000, warmup=100, per_kind=12, nmin=1e4, nmax=8e6,
            "requests": n_requests, "warmup": warmup, "budget_bytes": budget_bytes,
            "workers_per_server": workers, "max_batch": max_batch,
            "servers": "one service per kind (its own parameters), a third of the budget each",
+           "params": {"grid2d": C4_GRID2D_PARAMS, "grid3d": GRID3D_PARAMS, "rgg": RGG_PARAMS},
            "bases_per_kind": per_kind, "generate_s": round(t_gen, 1)}
     try:
         # capacity: requests with new matrices, one at a time

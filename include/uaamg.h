@@ -375,12 +375,11 @@ void uaamg_server_destroy(uaamg_server* s);
  * (A->on_device = 1).  Nothing is allocated: all scratch lives in one static device array
  * of about 19 MB that every GPU loading this library holds until the process exits, so
  * A->n may be at most 262,144 (larger graphs return UAAMG_ERR_UNSUPPORTED before any device
- * work).  The first call on a device looks up that array's address (cudaGetSymbolAddress)
- * and should therefore come before any stream capture.  Every call shares the array and
- * clears what must start at zero: calls whose work overlaps on the GPU (different streams,
- * or different host threads) race and must be serialised by the caller.  The call
- * synchronises `stream` three times (after validation, after the aggregation passes, and to
- * read *nc).
+ * work).  The first call on a device looks up that array's address (cudaGetSymbolAddress).
+ * Every call shares the array and clears what must start at zero: calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race and must be serialised by
+ * the caller.  The call synchronises `stream` three times (after validation, after the
+ * aggregation passes, and to read *nc).
  */
 int uaamg_aggregate_static(const uaamg_csr* A, int32_t max_agg_size, int32_t pass_mode,
                            uint64_t seed, int32_t* agg, int32_t* nc, void* stream);
