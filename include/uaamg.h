@@ -280,9 +280,11 @@ int uaamg_get_stats(const uaamg_handle* h, uaamg_stats* s);
 
 /*
  * Kernel timing hooks.  When enabled (params.profile_class at setup for the setup classes,
- * or uaamg_set_profiling before the first solve of a handle), every level-0
- * launch of the selected kernel class is bracketed by CUDA events on the launching stream
- * (inside the captured graphs as well), and the durations accumulate.
+ * or uaamg_set_profiling before the first solve of a handle), level-0 launches of the
+ * selected kernel class are bracketed by CUDA events on the launching stream and the
+ * durations accumulate: every such launch of the setup, and for the solve classes the
+ * launches of the first three outer iterations of each solve, which then run launch by
+ * launch (the remaining iterations run in the device-side loop, which holds no events).
  */
 #define UAAMG_KCLASS_SMOOTH0 1  /* level-0 first l1-Jacobi sweep + residual (fused SpMV) */
 #define UAAMG_KCLASS_SPMV64 2   /* level-0 FP64 SpMV + dot kernel of the outer iteration */

@@ -320,10 +320,15 @@ static int run_iteration(Handle* h, bool to_host = true) {
     return outer_iteration<double>(h, to_host);
 }
 
+// With a kernel class profiled, the first kProfIterations outer iterations of a solve run
+// launch by launch, their events recorded directly on the stream, and the rest run in the
+// device-side loop, whose conditional body cannot hold event nodes.
+constexpr int kProfIterations = 3;
+
 // The whole iteration loop as one graph: a while node whose body is one iteration followed
 // by k_outer_loop, which sets the node's condition on the device.  One launch runs every
-// iteration with no host round trip in between.  (Event nodes cannot sit in a conditional
-// body, so kernel-class profiling keeps the graph of one iteration.)
+// iteration with no host round trip in between.  The body is captured with kernel-class
+// profiling masked, so it holds no event nodes.
 static int ensure_loop_graph(Handle* h) {
     if (h->loop_graph) return UAAMG_OK;
     int st = UAAMG_OK;
@@ -347,6 +352,8 @@ static int ensure_loop_graph(Handle* h) {
     }
     if (st == UAAMG_OK) {
         cudaGraph_t body = np.conditional.phGraph_out[0];
+        const int prof_class = h->prof_class;
+        h->prof_class = 0;
         h->capturing = true;
         const long long nodes0 = h->graph_nodes;
         h->graph_nodes = 0;
@@ -361,6 +368,7 @@ static int ensure_loop_graph(Handle* h) {
         h->loop_nodes = h->graph_nodes;
         h->graph_nodes = nodes0;
         h->capturing = false;
+        h->prof_class = prof_class;
     }
     if (st == UAAMG_OK) st = check_cuda(cudaGraphInstantiate(&h->loop_graph, g, 0));
     cudaGraphDestroy(g);
@@ -397,66 +405,24 @@ static int iterate_loop(Handle* h, double stop_rr, int limit, int* done) {
     return st;
 }
 
-static int ensure_graph(Handle* h) {
-    if (h->graph || !h->p.use_graphs) return UAAMG_OK;
-    cudaGraph_t g = nullptr;
-    h->capturing = true;
-    h->graph_nodes = 0;
-    size_t slot0 = h->prof_slots.size();
-    int st = check_cuda(cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal));
-    if (st == UAAMG_OK) {
-        int st2 = run_iteration(h);
-        st = check_cuda(cudaStreamEndCapture(h->work, &g));
-        if (st2) st = st2;
-    }
-    h->capturing = false;
-    if (st == UAAMG_OK) st = check_cuda(cudaGraphInstantiate(&h->graph, g, 0));
-    if (g) cudaGraphDestroy(g);
-    if (st != UAAMG_OK) {
-        h->graph = nullptr;
-        h->prof_slots.resize(slot0);
-        cudaGetLastError();
-    }
-    return st;
-}
-
-static void harvest_profile(Handle* h) {
-    for (auto& ps : h->prof_slots) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ps.a, ps.b) == cudaSuccess) {
-            h->prof_ms += ms;
-            h->prof_launches++;
-        }
-    }
-    cudaGetLastError();
-}
-
-// Host-side readback of the scalars after an iteration (the copy is part of the iteration).
+// One iteration by direct launches, then the host-side readback of its scalars (the copy is
+// part of the iteration); the events of profiled launches are read and released here.
 static int iterate_once(Handle* h) {
-    int st;
-    if (h->graph) {
-        st = check_cuda(cudaGraphLaunch(h->graph, h->work));
-        count_launch(h, h->graph_nodes);
-    } else {
-        size_t s0 = h->prof_slots.size();
-        st = run_iteration(h);
-        if (st == UAAMG_OK) st = check_cuda(cudaStreamSynchronize(h->work));
-        if (st == UAAMG_OK && h->prof_class) {
-            for (size_t i = s0; i < h->prof_slots.size(); i++) {
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, h->prof_slots[i].a, h->prof_slots[i].b) == cudaSuccess) {
-                    h->prof_ms += ms;
-                    h->prof_launches++;
-                }
-                cudaEventDestroy(h->prof_slots[i].a);
-                cudaEventDestroy(h->prof_slots[i].b);
-            }
-            h->prof_slots.resize(s0);
-        }
-        return st;
-    }
+    size_t s0 = h->prof_slots.size();
+    int st = run_iteration(h);
     if (st == UAAMG_OK) st = check_cuda(cudaStreamSynchronize(h->work));
-    if (st == UAAMG_OK && h->prof_class) harvest_profile(h);
+    if (st == UAAMG_OK && h->prof_class) {
+        for (size_t i = s0; i < h->prof_slots.size(); i++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, h->prof_slots[i].a, h->prof_slots[i].b) == cudaSuccess) {
+                h->prof_ms += ms;
+                h->prof_launches++;
+            }
+            cudaEventDestroy(h->prof_slots[i].a);
+            cudaEventDestroy(h->prof_slots[i].b);
+        }
+        h->prof_slots.resize(s0);
+    }
     return st;
 }
 
@@ -519,9 +485,27 @@ int solve(Handle* h, const double* b, double* x, double tol, int use_guess, int*
     h->hist.push_back(rn / bn);
     if (rn <= tol * bn) status = UAAMG_OK;
     int k = 0;
-    const bool loop = h->p.use_graphs && !h->prof_class && h->osc_host->bb > 0.0;
-    if (status != UAAMG_OK && loop && (st = ensure_loop_graph(h))) return st;
-    while (loop && status != UAAMG_OK && k < h->p.max_iter) {
+    const bool loop = h->p.use_graphs && h->osc_host->bb > 0.0;
+    // iterations by direct launches, with a host round trip each: all of them without the
+    // device-side loop, else the profiled first ones
+    const int once = loop ? (h->prof_class ? kProfIterations : 0) : h->p.max_iter;
+    while (status != UAAMG_OK && k < h->p.max_iter && k < once) {
+        if ((st = iterate_once(h))) return st;
+        k++;
+        if (h->osc_host->breakdown) break;
+        rn = sqrt(h->osc_host->rr);
+        if (rn <= tol * bn) {
+            if ((st = true_residual(h))) return st;
+            rn = sqrt(h->osc_host->rr);
+            if (rn <= tol * bn) status = UAAMG_OK;
+        }
+        h->hist.push_back(rn / bn);
+    }
+    const bool broke = k > 0 && h->osc_host->breakdown;
+    if (status != UAAMG_OK && loop && !broke && k < h->p.max_iter &&
+        (st = ensure_loop_graph(h)))
+        return st;
+    while (loop && !broke && status != UAAMG_OK && k < h->p.max_iter) {
         // iterate on the device until the recursive residual passes, then confirm it
         int done = 0;
         const double stop_rr = (tol * bn) * (tol * bn);
@@ -535,19 +519,6 @@ int solve(Handle* h, const double* b, double* x, double tol, int use_guess, int*
             h->hist.back() = rn / bn;
             if (rn <= tol * bn) status = UAAMG_OK;
         }
-    }
-    if (!loop && status != UAAMG_OK && (st = ensure_graph(h))) return st;
-    while (!loop && status != UAAMG_OK && k < h->p.max_iter) {
-        if ((st = iterate_once(h))) return st;
-        k++;
-        if (h->osc_host->breakdown) break;
-        rn = sqrt(h->osc_host->rr);
-        if (rn <= tol * bn) {
-            if ((st = true_residual(h))) return st;
-            rn = sqrt(h->osc_host->rr);
-            if (rn <= tol * bn) status = UAAMG_OK;
-        }
-        h->hist.push_back(rn / bn);
     }
     if ((st = check_cuda(cudaMemcpyAsync(x, h->x, sizeof(double) * n, cudaMemcpyDefault, h->work))))
         return st;
